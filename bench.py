@@ -1,0 +1,325 @@
+"""Benchmark of the time-domain BEM hot path on one GB300.
+
+One "step" is one marching-on-in-time step (Eq. linear): the history sum
+that forms b^{a-1} over every stored element pair and lag, the incident-wave
+term, and the zero-lag solve.  The workload is the seeded synthetic
+scattering problem with Ns = 20480: a sound-hard ellipsoid (icosphere
+subdivision 5 mapped by axes ~ U[0.5, 1.5], seed 3), Burton-Miller BIE,
+B-spline order d = 2, c dt = 0.5 x mean edge, Gaussian plane pulse (sigma =
+0.3, seeded direction).  The path is the direct (all-pairs) FP64 history
+sum; the space-time FMM is not built yet, so the workload name says
+"direct".
+
+Before the W warm-up steps the run marches gamma_max steps untimed, so that
+every timed step uses the full lag window of every pair (steady state).
+The coefficient stream (~14 GB) is far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Output: one JSON line (see the keys below).  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ellipsoid20480_bmbie_d2_hard_plane"
+METRIC = "time-steps/sec FMM-TDBEM Ns=20480 (mixed vs FP64 form, ≤1e-3 rel L2); M2L TC util"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, n in enumerate(names):
+                    if r[3 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _excitation(w, xc, n, alphas):
+    """Host-side excitation e_i(t_a) of the sound-hard Burton-Miller problem:
+    (d/dn_x - c^-1 d/dt) of the Gaussian plane pulse, the caller's input in
+    the end-to-end measurement."""
+    k = np.asarray(w.direction, dtype=np.float64)
+    kx = xc @ k
+    kn = n @ k
+    out = np.empty((len(alphas), len(xc)))
+    for r, a in enumerate(alphas):
+        s = (a * w.dt - w.t0 - kx / w.c) / w.sigma
+        df = -2.0 * s / w.sigma * np.exp(-s * s)
+        out[r] = -(1.0 + kn) / w.c * df
+    return out
+
+
+def _geometry(w):
+    v = w.xyz[w.tri]
+    xc = (v[:, 0] + v[:, 1] + v[:, 2]) / 3.0
+    g = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    return xc, -g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2111_05205_gb300 import abi, build
+    from synth import workload
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+
+    w = workload(args.workload)
+    from paper_2111_05205_gb300 import Solver
+    # spin-up + warm-up + timed (device) + timed (e2e) steps must fit in Nt-1
+    probe_gmax = 260
+    need = probe_gmax + 2 * (args.warmup + args.steps) + 2
+    w.nt = max(w.nt, need)
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.time()
+    phi = np.full(w.ns, 1 if w.bc == "neumann" else 0, np.int8)
+    s = Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi,
+               incident=(w.direction, w.t0, w.sigma), stream=stream)
+    setup_s = time.time() - t0
+    st0 = s.stats()
+    gmax = st0["gamma_max"]
+    ctx = s.ctx
+    # spin-up to steady state, then warm-up
+    abi.tdbem_step(ctx, gmax)
+    abi.tdbem_step(ctx, args.warmup)
+    abi.tdbem_sync(ctx)
+    abi.tdbem_reset_stats(ctx)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        abi.tdbem_step(ctx, args.steps)
+        ev1.record()
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = s.stats()
+    abi.tdbem_sync(ctx)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+
+    # end to end through the C ABI with host buffers: per step, the
+    # excitation goes host -> device and the solution device -> host
+    a_start = abi.tdbem_steps_done(ctx) + 1
+    n_e2e = args.warmup + args.steps
+    xc, nrm = _geometry(w)
+    exc = torch.from_numpy(_excitation(w, xc, nrm, range(a_start, a_start + n_e2e))).pin_memory()
+    xout = torch.empty((n_e2e, w.ns), dtype=torch.float64).pin_memory()
+    for r in range(args.warmup):
+        abi.tdbem_step_io(ctx, 1, exc[r], xout[r], on_device=False)
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    for r in range(args.warmup, n_e2e):
+        abi.tdbem_step_io(ctx, 1, exc[r], xout[r], on_device=False)
+    e2e_s = time.perf_counter() - t_e
+    assert np.isfinite(xout.numpy()).all()
+
+    hbm, peak_kind = _peaks()
+    near_ms = st["ms_near"] / max(st["launches_near"], 1)
+    achieved = st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9
+    launches = (st["launches_near"] + st["launches_solve"]) 
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "near_sum_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            if tr.get("kernel_rev") == _kernel_rev():
+                traffic = tr["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    out = {
+        "metric": METRIC,
+        "value": world * 1000.0 / ms_step,
+        "unit": "time-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + "_direct_fp64", "ns": w.ns, "d": w.d, "bie": w.bie, "bc": w.bc,
+                   "gamma_max": gmax, "spinup_steps": gmax, "coefficients_per_kind": st["n_coef"],
+                   "l2": "working set (%.1f GB per step) larger than L2; no flush" %
+                         (st["near_bytes_per_step"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single-gpu", "setup_s": round(setup_s, 2)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "kernel": "k_near_sum", "peak_source": peak_kind,
+                     "bytes_per_launch": st["near_bytes_per_step"], "avg_launch_ms": near_ms},
+        "phases_ms_per_step": {"near": near_ms, "solve": st["ms_solve"] / max(st["steps"], 1),
+                               "solve_sweeps": st["solve_iters"]},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "time-steps/s",
+                "h2d_bytes_per_step": w.ns * 8, "d2h_bytes_per_step": w.ns * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    s.close()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, rows=args.cpu_rows)
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _kernel_rev():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("march.cu", "tdbem_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def cpu_baseline(w, rows=4, repeats=3):
+    """The FP64 oracle on the host cores, on a bounded sample of the
+    workload: the history sum of ``rows`` observation rows over every lag
+    and every source element (its step loop, Eq. linear, restricted to those
+    rows), scaled to all Ns rows; the rows' coefficients are the oracle's
+    (computed first, untimed)."""
+    from oracle import coeffs as oc
+    cdt = w.c * w.dt
+    gm = oc.gamma_max(w.xyz, w.tri, w.d, cdt)
+    rng = np.random.default_rng(0)
+    rsel = np.sort(rng.choice(w.ns, size=rows, replace=False))
+    kind = "wb" if w.bc == "neumann" else "ub"
+    C = oc.rows(w.xyz, w.tri, w.d, cdt, rsel, kinds=(kind,), gmax=gm)[kind]  # [r, g, j]
+    hist = np.random.default_rng(1).standard_normal((gm + 1, w.ns))
+    ts = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        b = np.zeros(rows)
+        for g in range(1, gm + 1):
+            b += C[:, g, :] @ hist[gm - g]
+        ts.append(time.perf_counter() - t)
+    per_step = min(ts) * w.ns / rows
+    return {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": oc.num_threads(), "kind": "oracle",
+            "sample": "history sum of %d of %d rows over all %d lags (oracle dense rows, numpy), scaled x%.0f"
+                      % (rows, w.ns, gm, w.ns / rows)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import workload
+    w = workload(args.workload)
+    rows = args.cpu_rows
+    samples = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, rows=rows, repeats=1)
+        if k >= args.warmup:
+            samples.append(1.0 / cb["value"])
+    per_step = float(np.mean(samples))
+    out = {"metric": METRIC, "value": 1.0 / per_step, "unit": "time-steps/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD + "_direct_fp64", "ns": w.ns},
+           "cpu_baseline": {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": cb["cores"],
+                            "kind": "oracle", "sample": cb["sample"]},
+           "e2e": {"value": 1.0 / per_step, "unit": "time-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-rows", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

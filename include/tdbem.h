@@ -1,0 +1,183 @@
+/*
+ * tdbem.h -- C ABI of the GB300 time-domain boundary element library.
+ *
+ * The library solves the exterior initial-boundary value problem of the 3-D
+ * scalar wave equation (Section 2.1, Eq. ibvp) by the time-domain boundary
+ * element method of Takahashi, Tanigawa & Miyazawa (arXiv 2111.05205):
+ * piecewise-constant elements with centroid collocation in space and
+ * uniform-knot B-splines of order d in time (Section 2.3, Eq. u_bspline), the
+ * ordinary BIE (Eq. bie, "OBIE") or the Burton-Miller BIE (Eq. bmbie,
+ * "BMBIE"), marched in time step by step (Section 2.5, Eq. linear).
+ *
+ * Conventions common to every call:
+ *   - every call returns an int status (tdbem_status); nothing throws;
+ *   - inputs are copied, the caller keeps ownership of its buffers;
+ *   - outputs go to caller-allocated buffers (host, or device memory of the
+ *     context's GPU when a call takes on_device = 1);
+ *   - the CUDA stream given to tdbem_create is borrowed, never destroyed;
+ *     all device work of a context is ordered after the work queued on that
+ *     stream before the call and before work queued on it after the call;
+ *   - a context owns all the device memory it allocates (cudaMalloc) and
+ *     frees it in tdbem_destroy; there is no global mutable state;
+ *   - tdbem_last_error returns a message for the last failed call of the
+ *     context (a static string for a NULL context).
+ *
+ * Units and signs (readings of the paper where it is silent):
+ *   - mesh triangles are ordered counter-clockwise seen from outside the
+ *     scatterer V; the paper's normal n (Eq. bie) points INTO V, i.e. it is
+ *     minus the geometric normal (v1-v0)x(v2-v0) normalised;
+ *   - q = du/dn with that n;
+ *   - the collocation point x_i is the centroid (v0+v1+v2)/3 of element i;
+ *   - the free term is absorbed into the double layer by evaluating every
+ *     coefficient as the limit of x_i approaching S from outside V
+ *     (Section 2.4, below Eq. bie_disc').
+ *   - the incident wave (omitted from the formulation in Section 2.1) enters
+ *     as the total-field term: 0 = e_i(t_a) + sum_j sum_b (Ubar q - Wbar u),
+ *     with e = u_in (OBIE) or e = (d/dn_x - c^-1 d/dt) u_in (BMBIE).
+ */
+#ifndef TDBEM_H
+#define TDBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdbem_ctx tdbem_ctx;
+
+typedef enum {
+    TDBEM_OK = 0,
+    TDBEM_ERR_ARG = -1,        /* invalid argument or size */
+    TDBEM_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    TDBEM_ERR_OOM = -3,        /* device allocation failed */
+    TDBEM_ERR_NOT_CONVERGED = -4,
+    TDBEM_ERR_DIVERGED = -5,   /* solution norm grew past the guard */
+    TDBEM_ERR_TIMEOUT = -6,
+    TDBEM_ERR_INFEASIBLE_HIERARCHY = -7,
+    TDBEM_ERR_STATE = -8       /* call out of order (e.g. step before prepare) */
+} tdbem_status;
+
+/* Problem and method parameters (Section 2, Section 5.1 for the values the
+ * paper uses). */
+typedef struct {
+    double c;             /* wave speed c > 0 */
+    double dt;            /* time-step length Delta_t > 0 */
+    int32_t nt;           /* number of time steps Nt >= 2; collocation at t_a, a = 1..Nt-1 */
+    int32_t d;            /* B-spline order d, 1 <= d <= 4 (Eq. decompose) */
+    int32_t bie;          /* 0 = OBIE (Eq. bie), 1 = BMBIE (Eq. bmbie) */
+    int32_t algo;         /* 0 = direct history sum over all element pairs (Eq. linear) */
+    int32_t precision;    /* 0 = FP64 throughout */
+    int32_t ps, pt, mu, depth; /* space-time FMM parameters; unused by algo 0 */
+    double solver_tol;    /* bound on the zero-lag solve's relative error (0: 1e-16) */
+    int32_t solver_maxit; /* cap on zero-lag iterations (0: 200) */
+    int32_t reserved;
+} tdbem_params;
+
+/* Per-phase device time (ms) and launch counts accumulated since the last
+ * tdbem_reset_stats; filled by tdbem_get_stats, which synchronises. */
+typedef struct {
+    double ms_rhs, ms_near, ms_solve, ms_total;
+    int64_t launches_rhs, launches_near, launches_solve;
+    int64_t steps;                 /* time steps taken in total */
+    int64_t n_pairs;               /* element pairs with a non-empty lag window */
+    int64_t n_coef;                /* stored coefficients per kind */
+    int64_t near_bytes_per_step;   /* algorithmic HBM bytes of one full history sum: every
+                                      stored coefficient, the pair windows (2 B per pair),
+                                      block offsets (8 B per 32 pairs), the history window
+                                      (gamma_max x ns x 8 B per history kind) and b */
+    int32_t gamma_max;             /* largest lag stored */
+    int32_t solve_iters;           /* zero-lag iterations per step */
+    double solve_contraction;      /* max_i sum_{j!=i} |A_ij / A_ii| */
+    double ms_prepare;             /* wall time of tdbem_prepare */
+} tdbem_stats;
+
+/* Creates a context on the current CUDA device.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream) on which the caller orders its work. */
+int tdbem_create(const tdbem_params *params, void *stream, tdbem_ctx **out);
+
+/* Frees all device and host memory of the context (NULL is a no-op). */
+void tdbem_destroy(tdbem_ctx *ctx);
+
+/* Message of the last failed call ("" if none). */
+const char *tdbem_last_error(const tdbem_ctx *ctx);
+
+/* Surface mesh (Section 2.3): xyz[nv*3] vertex coordinates, tri[ns*3]
+ * vertex indices of the ns flat triangular elements, counter-clockwise seen
+ * from outside V.  Host pointers, copied.  ERR_ARG on an index out of range
+ * or a degenerate triangle. */
+int tdbem_set_mesh(tdbem_ctx *ctx, const double *xyz, int32_t nv, const int32_t *tri, int32_t ns);
+
+/* Boundary condition per element (Section 2.5, phi_j): phi[ns] host, 1 =
+ * Neumann (q given, u unknown), 0 = Dirichlet (u given, q unknown).
+ * Default: all 0. */
+int tdbem_set_bc(tdbem_ctx *ctx, const int8_t *phi);
+
+/* Known boundary data sampled at the collocation times: f[(Nt-1)*ns] host,
+ * row a-1 (a = 1..Nt-1) holds u_j(t_a) where phi_j = 0 and q_j(t_a) where
+ * phi_j = 1.  tdbem_prepare converts the samples to B-spline coefficients
+ * (Eq. u_bspline) by collocation, sum_{g=1..d} N^{0,d}(g) fbar^{a-g} = f(t_a),
+ * marched in a (a reading: the paper does not say how known data is
+ * expanded; for d = 1 it gives fbar^{a-1} = f(t_a)).  NULL = homogeneous
+ * (the default).  ERR_ARG on a non-finite sample. */
+int tdbem_set_known(tdbem_ctx *ctx, const double *f);
+
+/* Incident plane pulse u_in(x,t) = f(t - t0 - k.x/c), f(s) = exp(-(s/width)^2)
+ * (shape 0), k = dir normalised.  Replaces nothing else; without this call
+ * there is no incident wave. */
+int tdbem_set_incident_plane(tdbem_ctx *ctx, const double dir[3], double t0, double width, int32_t shape);
+
+/* Builds everything the marching needs on the device: element geometry,
+ * lag windows, influence coefficients (Section 2.4, Appendix B), the
+ * zero-lag matrix A (Eq. linear).  Synchronous. */
+int tdbem_prepare(tdbem_ctx *ctx);
+
+/* Advances nsteps time steps (Eq. linear at a = a_cur+1 .. a_cur+nsteps,
+ * a <= Nt-1).  Asynchronous on the context's stream; ERR_ARG past Nt-1. */
+int tdbem_step(tdbem_ctx *ctx, int32_t nsteps);
+
+/* Advances nsteps time steps with the excitation supplied by the caller:
+ * exc[nsteps*ns] holds the excitation e_i(t_a) of the steps taken (used in
+ * place of the configured incident-wave term), and x_out[nsteps*ns]
+ * receives the unknown x^{a-1}
+ * of each step.  on_device = 0: both are host buffers (pinned or pageable)
+ * and the call copies in and out on the stream and returns after the
+ * copies completed; on_device = 1: device buffers, asynchronous.  exc may
+ * be NULL (the configured incident wave, if any, is used); x_out may be
+ * NULL. */
+int tdbem_step_io(tdbem_ctx *ctx, int32_t nsteps, const double *exc, double *x_out, int32_t on_device);
+
+/* Number of time steps taken so far (a_cur). */
+int tdbem_steps_done(const tdbem_ctx *ctx, int32_t *out);
+
+/* B-spline coefficient histories u_j^beta, q_j^beta for beta = beta0 ..
+ * beta0+nbeta-1 (each [nbeta*ns], either may be NULL).  Synchronises. */
+int tdbem_get_solution(const tdbem_ctx *ctx, double *u, double *q, int32_t beta0, int32_t nbeta, int32_t on_device);
+
+/* Right-hand side b^{a-1} of the last step taken (Eq. linear, incident term
+ * included), b[ns] host.  Synchronises. */
+int tdbem_get_rhs(const tdbem_ctx *ctx, double *b);
+
+/* Stored influence coefficients of selected rows, expanded to dense form:
+ * kind 0 = C_U, 1 = C_W, 2 = Ubar, 3 = Wbar (only the kinds the run needs are
+ * stored; ERR_ARG for another); rows[nrows] element indices;
+ * out[nrows*(gmax+1)*ns] host, out[(r*(gmax+1)+g)*ns + j], zero outside the
+ * stored windows and at g = 0. */
+int tdbem_get_coefficients(const tdbem_ctx *ctx, int32_t kind, const int32_t *rows, int32_t nrows,
+                           int32_t gmax, double *out);
+
+/* Zero-lag matrix A of Eq. linear as dense host rows out[ns*ns] (small ns only). */
+int tdbem_get_zero_lag(const tdbem_ctx *ctx, double *out);
+
+int tdbem_get_stats(const tdbem_ctx *ctx, tdbem_stats *out);
+int tdbem_reset_stats(tdbem_ctx *ctx);
+
+/* Blocks until all work of the context has finished; reports a device-side
+ * error (divergence guard) raised since the last check. */
+int tdbem_sync(tdbem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDBEM_H */

@@ -1,0 +1,202 @@
+"""ctypes binding of libtdbem's C ABI (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: the time marching, the coefficients and the solve
+all run in the CUDA library.  Status codes other than TDBEM_OK raise
+``TdbemError``.  The library must have been built (``build.build()``); if it
+is missing, loading fails loudly -- there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TDBEM_OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NOT_CONVERGED", -5: "ERR_DIVERGED",
+          -6: "ERR_TIMEOUT", -7: "ERR_INFEASIBLE_HIERARCHY", -8: "ERR_STATE"}
+
+
+class TdbemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class tdbem_params(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("nt", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("bie", ctypes.c_int32), ("algo", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("ps", ctypes.c_int32), ("pt", ctypes.c_int32), ("mu", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("solver_tol", ctypes.c_double), ("solver_maxit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class tdbem_stats(ctypes.Structure):
+    _fields_ = [("ms_rhs", ctypes.c_double), ("ms_near", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("launches_rhs", ctypes.c_int64),
+                ("launches_near", ctypes.c_int64), ("launches_solve", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64), ("n_coef", ctypes.c_int64), ("near_bytes_per_step", ctypes.c_int64),
+                ("gamma_max", ctypes.c_int32), ("solve_iters", ctypes.c_int32),
+                ("solve_contraction", ctypes.c_double), ("ms_prepare", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_D = ctypes.c_double
+# name -> (restype, argtypes); the declarations of include/tdbem.h
+SIGNATURES = {
+    "tdbem_create": (ctypes.c_int, [ctypes.POINTER(tdbem_params), _P, ctypes.POINTER(_P)]),
+    "tdbem_destroy": (None, [_P]),
+    "tdbem_last_error": (ctypes.c_char_p, [_P]),
+    "tdbem_set_mesh": (ctypes.c_int, [_P, _P, _I, _P, _I]),
+    "tdbem_set_bc": (ctypes.c_int, [_P, _P]),
+    "tdbem_set_known": (ctypes.c_int, [_P, _P]),
+    "tdbem_set_incident_plane": (ctypes.c_int, [_P, _P, _D, _D, _I]),
+    "tdbem_prepare": (ctypes.c_int, [_P]),
+    "tdbem_step": (ctypes.c_int, [_P, _I]),
+    "tdbem_step_io": (ctypes.c_int, [_P, _I, _P, _P, _I]),
+    "tdbem_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_I)]),
+    "tdbem_get_solution": (ctypes.c_int, [_P, _P, _P, _I, _I, _I]),
+    "tdbem_get_rhs": (ctypes.c_int, [_P, _P]),
+    "tdbem_get_coefficients": (ctypes.c_int, [_P, _I, _P, _I, _I, _P]),
+    "tdbem_get_zero_lag": (ctypes.c_int, [_P, _P]),
+    "tdbem_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(tdbem_stats)]),
+    "tdbem_reset_stats": (ctypes.c_int, [_P]),
+    "tdbem_sync": (ctypes.c_int, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libtdbem.so (built in-tree); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libtdbem.so is not built (%s); run paper_2111_05205_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _check(ctx, code):
+    if code != TDBEM_OK:
+        msg = lib().tdbem_last_error(ctx)
+        raise TdbemError(code, msg.decode() if msg else "")
+
+
+def tdbem_create(params, stream=None):
+    out = _P()
+    code = lib().tdbem_create(ctypes.byref(params), stream, ctypes.byref(out))
+    if code != TDBEM_OK:
+        raise TdbemError(code, "tdbem_create")
+    return out.value
+
+
+def tdbem_destroy(ctx):
+    lib().tdbem_destroy(ctx)
+
+
+def tdbem_last_error(ctx):
+    m = lib().tdbem_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def tdbem_set_mesh(ctx, xyz, tri):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    _check(ctx, lib().tdbem_set_mesh(ctx, _ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0]))
+
+
+def tdbem_set_bc(ctx, phi):
+    phi = np.ascontiguousarray(phi, dtype=np.int8)
+    _check(ctx, lib().tdbem_set_bc(ctx, _ptr(phi)))
+
+
+def tdbem_set_known(ctx, f):
+    """f: known samples [(nt-1), ns] at t_1 .. t_{nt-1}, or None."""
+    k = None if f is None else np.ascontiguousarray(f, dtype=np.float64)
+    _check(ctx, lib().tdbem_set_known(ctx, _ptr(k)))
+
+
+def tdbem_set_incident_plane(ctx, direction, t0, width, shape=0):
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    _check(ctx, lib().tdbem_set_incident_plane(ctx, _ptr(d), float(t0), float(width), int(shape)))
+
+
+def tdbem_prepare(ctx):
+    _check(ctx, lib().tdbem_prepare(ctx))
+
+
+def tdbem_step(ctx, nsteps):
+    _check(ctx, lib().tdbem_step(ctx, int(nsteps)))
+
+
+def tdbem_step_io(ctx, nsteps, exc=None, x_out=None, on_device=False):
+    """exc / x_out: numpy arrays (host) or torch CUDA tensors (on_device)."""
+    _check(ctx, lib().tdbem_step_io(ctx, int(nsteps), _ptr(exc), _ptr(x_out), int(bool(on_device))))
+
+
+def tdbem_steps_done(ctx):
+    v = _I()
+    _check(ctx, lib().tdbem_steps_done(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def tdbem_get_solution(ctx, ns, beta0, nbeta):
+    u = np.zeros((nbeta, ns))
+    q = np.zeros((nbeta, ns))
+    _check(ctx, lib().tdbem_get_solution(ctx, _ptr(u), _ptr(q), int(beta0), int(nbeta), 0))
+    return u, q
+
+
+def tdbem_get_rhs(ctx, ns):
+    b = np.zeros(ns)
+    _check(ctx, lib().tdbem_get_rhs(ctx, _ptr(b)))
+    return b
+
+
+def tdbem_get_coefficients(ctx, kind, rows, gmax, ns):
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.zeros((len(rows), gmax + 1, ns))
+    _check(ctx, lib().tdbem_get_coefficients(ctx, int(kind), _ptr(rows), len(rows), int(gmax), _ptr(out)))
+    return out
+
+
+def tdbem_get_zero_lag(ctx, ns):
+    out = np.zeros((ns, ns))
+    _check(ctx, lib().tdbem_get_zero_lag(ctx, _ptr(out)))
+    return out
+
+
+def tdbem_get_stats(ctx):
+    s = tdbem_stats()
+    _check(ctx, lib().tdbem_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def tdbem_reset_stats(ctx):
+    _check(ctx, lib().tdbem_reset_stats(ctx))
+
+
+def tdbem_sync(ctx):
+    _check(ctx, lib().tdbem_sync(ctx))

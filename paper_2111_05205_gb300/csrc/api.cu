@@ -1,0 +1,593 @@
+// C ABI of libtdbem: context life cycle, setup (tdbem_prepare) and the
+// time-marching driver (Section 2.5, Eq. linear).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "tdbem_internal.cuh"
+
+using namespace tdbem;
+
+namespace {
+
+int fail(tdbem_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define TD_CUDA(call)                                                                                    \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? TDBEM_ERR_OOM : TDBEM_ERR_CUDA,             \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(tdbem_ctx *c, T **p, size_t n)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+    if (e == cudaSuccess) {
+        c->allocs.push_back(q);
+        *p = (T *)q;
+    }
+    return e;
+}
+
+void dfree(tdbem_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+// Orders the context's stream after the user's stream (call entry) and the
+// user's stream after the context's stream (call exit).
+cudaError_t join(cudaStream_t from, cudaStream_t to)
+{
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (r != cudaSuccess) return r;
+    r = cudaEventRecord(e, from);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(to, e, 0);
+    cudaEventDestroy(e);
+    return r;
+}
+
+cudaEvent_t take_event(tdbem_ctx *c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Accumulates the elapsed times of all recorded phase intervals (waits for
+// them).
+void harvest(tdbem_ctx *c)
+{
+    for (auto &p : c->pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->ms[p.phase] += ms;
+        c->pool.push_back(p.a);
+        c->pool.push_back(p.b);
+    }
+    c->pending.clear();
+}
+
+struct PhaseTimer {
+    tdbem_ctx *c;
+    int phase;
+    cudaEvent_t a;
+    PhaseTimer(tdbem_ctx *c_, int ph) : c(c_), phase(ph)
+    {
+        if (c->pending.size() > 8192) harvest(c);
+        a = take_event(c);
+        cudaEventRecord(a, c->s);
+    }
+    ~PhaseTimer()
+    {
+        cudaEvent_t b = take_event(c);
+        cudaEventRecord(b, c->s);
+        c->pending.push_back({phase, a, b});
+    }
+};
+
+int check_flags(tdbem_ctx *c)
+{
+    int f = 0;
+    TD_CUDA(cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & 1) return fail(c, TDBEM_ERR_DIVERGED, "non-finite solution value (divergence guard)");
+    return TDBEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdbem_create(const tdbem_params *p, void *stream, tdbem_ctx **out)
+{
+    tdbem_ctx *c = nullptr;
+    if (!p || !out) return TDBEM_ERR_ARG;
+    *out = nullptr;
+    if (!(p->c > 0) || !(p->dt > 0) || p->nt < 2 || p->d < 1 || p->d > kMaxD || (p->bie != 0 && p->bie != 1) ||
+        p->algo != 0 || p->precision != 0)
+        return TDBEM_ERR_ARG;
+    c = new tdbem_ctx();
+    c->P = *p;
+    c->cdt = p->c * p->dt;
+    c->user = (cudaStream_t)stream;
+    cudaGetDevice(&c->dev);
+    if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return TDBEM_ERR_CUDA;
+    }
+    bspline_table(p->d, &c->bs);
+    c->inc.on = 0;
+    c->inc.bie = p->bie;
+    c->inc.c = p->c;
+    c->inc.dt = p->dt;
+    if (dalloc(c, &c->d_flag, 4) != cudaSuccess) {
+        tdbem_destroy(c);
+        return TDBEM_ERR_OOM;
+    }
+    cudaMemset(c->d_flag, 0, 4 * sizeof(int));
+    *out = c;
+    return TDBEM_OK;
+}
+
+void tdbem_destroy(tdbem_ctx *c)
+{
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    harvest(c);
+    for (auto e : c->pool) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->s) cudaStreamDestroy(c->s);
+    delete c;
+}
+
+const char *tdbem_last_error(const tdbem_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int tdbem_set_mesh(tdbem_ctx *c, const double *xyz, int32_t nv, const int32_t *tri, int32_t ns)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    if (c->prepared) return fail(c, TDBEM_ERR_STATE, "mesh set after prepare");
+    if (!xyz || !tri || nv < 3 || ns < 1) return fail(c, TDBEM_ERR_ARG, "empty mesh");
+    for (int64_t k = 0; k < 3 * (int64_t)ns; ++k)
+        if (tri[k] < 0 || tri[k] >= nv) return fail(c, TDBEM_ERR_ARG, "triangle vertex index out of range");
+    for (int i = 0; i < ns; ++i) {
+        const double *a = xyz + 3 * tri[3 * i], *b = xyz + 3 * tri[3 * i + 1], *d = xyz + 3 * tri[3 * i + 2];
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        double l2 = sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+        if (!(sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]) > 1e-12 * l1 * l2))
+            return fail(c, TDBEM_ERR_ARG, "degenerate triangle " + std::to_string(i));
+    }
+    c->nv = nv;
+    c->ns = ns;
+    c->xyz.assign(xyz, xyz + 3 * (int64_t)nv);
+    c->tri.assign(tri, tri + 3 * (int64_t)ns);
+    c->phi.assign(ns, 0);
+    c->kbar.clear();
+    return TDBEM_OK;
+}
+
+int tdbem_set_bc(tdbem_ctx *c, const int8_t *phi)
+{
+    if (!c || !phi) return TDBEM_ERR_ARG;
+    if (c->prepared) return fail(c, TDBEM_ERR_STATE, "bc set after prepare");
+    if (c->ns == 0) return fail(c, TDBEM_ERR_STATE, "bc before mesh");
+    for (int i = 0; i < c->ns; ++i)
+        if (phi[i] != 0 && phi[i] != 1) return fail(c, TDBEM_ERR_ARG, "phi must be 0 or 1");
+    c->phi.assign(phi, phi + c->ns);
+    return TDBEM_OK;
+}
+
+int tdbem_set_known(tdbem_ctx *c, const double *f)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    if (c->prepared) return fail(c, TDBEM_ERR_STATE, "known data set after prepare");
+    if (c->ns == 0) return fail(c, TDBEM_ERR_STATE, "known data before mesh");
+    if (!f) {
+        c->kbar.clear();
+        return TDBEM_OK;
+    }
+    int64_t n = (int64_t)(c->P.nt - 1) * c->ns;
+    for (int64_t k = 0; k < n; ++k)
+        if (!isfinite(f[k])) return fail(c, TDBEM_ERR_ARG, "non-finite known data");
+    c->kbar.assign(f, f + n);
+    return TDBEM_OK;
+}
+
+int tdbem_set_incident_plane(tdbem_ctx *c, const double dir[3], double t0, double width, int32_t shape)
+{
+    if (!c || !dir) return TDBEM_ERR_ARG;
+    if (shape != 0) return fail(c, TDBEM_ERR_ARG, "only the Gaussian pulse (shape 0) is implemented");
+    double l = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(l > 0) || !(width > 0)) return fail(c, TDBEM_ERR_ARG, "bad direction or width");
+    c->inc.on = 1;
+    for (int k = 0; k < 3; ++k) c->inc.k[k] = dir[k] / l;
+    c->inc.t0 = t0;
+    c->inc.width = width;
+    return TDBEM_OK;
+}
+
+int tdbem_prepare(tdbem_ctx *c)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    if (c->prepared) return fail(c, TDBEM_ERR_STATE, "already prepared");
+    if (c->ns == 0) return fail(c, TDBEM_ERR_STATE, "no mesh");
+    auto t_start = std::chrono::steady_clock::now();
+    const int ns = c->ns, nt = c->P.nt;
+    TD_CUDA(cudaSetDevice(c->dev));
+    TD_CUDA(join(c->user, c->s));
+    set_bspline_table(c->bs, c->s);
+
+    // which histories can be non-zero, hence which coefficient kinds
+    bool any_d = false, any_n = false;
+    for (int i = 0; i < ns; ++i) (c->phi[i] ? any_n : any_d) = true;
+    bool has_k = !c->kbar.empty();
+    bool q_nz = any_d || (has_k && any_n);
+    bool u_nz = any_n || (has_k && any_d);
+    c->ku_kind = q_nz ? (c->P.bie ? KIND_UB : KIND_CU) : -1;
+    c->kw_kind = u_nz ? (c->P.bie ? KIND_WB : KIND_CW) : -1;
+
+    // geometry
+    TD_CUDA(dalloc(c, &c->d_xyz, 3 * (size_t)c->nv));
+    TD_CUDA(dalloc(c, &c->d_tri, 3 * (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_V, 9 * (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_X, 3 * (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_xc, 3 * (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_n, 3 * (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_phi, (size_t)ns));
+    TD_CUDA(cudaMemcpyAsync(c->d_xyz, c->xyz.data(), 3 * sizeof(double) * c->nv, cudaMemcpyHostToDevice, c->s));
+    TD_CUDA(cudaMemcpyAsync(c->d_tri, c->tri.data(), 3 * sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->s));
+    TD_CUDA(cudaMemcpyAsync(c->d_phi, c->phi.data(), ns, cudaMemcpyHostToDevice, c->s));
+    TD_CUDA(launch_geometry(c));
+
+    // lag windows of all pairs
+    c->nblk = (ns + 31) / 32;
+    TD_CUDA(dalloc(c, &c->d_meta, (size_t)ns * ns));
+    int *d_m = c->d_flag + 1;  // flag[1..3]: max cnt, max g0, max lag
+    TD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->s));
+    TD_CUDA(launch_windows(c, d_m, d_m + 1, d_m + 2));
+    int mx[3];
+    TD_CUDA(cudaMemcpyAsync(mx, d_m, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    if (mx[0] > kMaxCnt) return fail(c, TDBEM_ERR_ARG, "lag window longer than 15 (element larger than ~10 c*dt)");
+    if (mx[1] > kMaxG0) return fail(c, TDBEM_ERR_ARG, "lag beyond 4095 (surface too large for c*dt)");
+    c->smax = mx[0];
+    c->gmax = mx[2];
+
+    // packed coefficient layout: per 32-pair block totals, prefix on the host
+    size_t nb = (size_t)ns * c->nblk;
+    TD_CUDA(dalloc(c, &c->d_btot, nb));
+    TD_CUDA(dalloc(c, &c->d_boff, nb));
+    TD_CUDA(launch_block_totals(c));
+    std::vector<int32_t> tot(nb);
+    std::vector<int64_t> off(nb);
+    TD_CUDA(cudaMemcpyAsync(tot.data(), c->d_btot, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    int64_t run = 0;
+    for (size_t k = 0; k < nb; ++k) {
+        off[k] = run;
+        run += tot[k];
+    }
+    c->ncoef = run;
+    c->npairs = (int64_t)ns * ns;
+    TD_CUDA(cudaMemcpyAsync(c->d_boff, off.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+
+    // influence coefficients
+    if (c->ku_kind >= 0) TD_CUDA(dalloc(c, &c->d_ku, (size_t)c->ncoef));
+    if (c->kw_kind >= 0) TD_CUDA(dalloc(c, &c->d_kw, (size_t)c->ncoef));
+    TD_CUDA(launch_coefficients(c));
+
+    // zero-lag matrix and its Jacobi contraction factor
+    TD_CUDA(dalloc(c, &c->d_aoff, (size_t)kEllWidth * ns));
+    TD_CUDA(dalloc(c, &c->d_acol, (size_t)kEllWidth * ns));
+    TD_CUDA(dalloc(c, &c->d_ainv, (size_t)ns));
+    TD_CUDA(launch_zero_lag(c));
+    std::vector<double> aoff((size_t)kEllWidth * ns), ainv(ns);
+    std::vector<int32_t> acol((size_t)kEllWidth * ns);
+    int fl = 0;
+    TD_CUDA(cudaMemcpyAsync(aoff.data(), c->d_aoff, aoff.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaMemcpyAsync(acol.data(), c->d_acol, acol.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaMemcpyAsync(ainv.data(), c->d_ainv, ainv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaMemcpyAsync(&fl, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    if (fl & 2) return fail(c, TDBEM_ERR_ARG, "zero-lag row with more than 8 off-diagonal entries");
+    if (fl & 4) return fail(c, TDBEM_ERR_ARG, "zero-lag matrix has a zero diagonal entry");
+    double qmax = 0.0;
+    for (int i = 0; i < ns; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < kEllWidth; ++k)
+            if (acol[(size_t)k * ns + i] >= 0) s += fabs(aoff[(size_t)k * ns + i]);
+        qmax = std::max(qmax, s * fabs(ainv[i]));
+    }
+    c->contraction = qmax;
+    double tol = c->P.solver_tol > 0 ? c->P.solver_tol : 1e-16;
+    int maxit = c->P.solver_maxit > 0 ? c->P.solver_maxit : 200;
+    if (!(qmax < 1.0))
+        return fail(c, TDBEM_ERR_NOT_CONVERGED,
+                    "zero-lag matrix not diagonally dominant (contraction " + std::to_string(qmax) + ")");
+    // Jacobi error after K sweeps (the first gives D^-1 b) <= q^K |x|
+    int K = (qmax > 0.0) ? (int)ceil(log(tol) / log(qmax)) : 1;
+    if (K < 1) K = 1;
+    if (K > maxit) return fail(c, TDBEM_ERR_NOT_CONVERGED, "zero-lag solve needs more sweeps than solver_maxit");
+    c->solve_iters = K;
+
+    // histories, initialised with the known data (unknown components zero)
+    size_t nh = (size_t)nt * ns;
+    TD_CUDA(dalloc(c, &c->d_u, nh));
+    TD_CUDA(dalloc(c, &c->d_q, nh));
+    TD_CUDA(cudaMemsetAsync(c->d_u, 0, nh * sizeof(double), c->s));
+    TD_CUDA(cudaMemsetAsync(c->d_q, 0, nh * sizeof(double), c->s));
+    if (has_k) {
+        double *d_f = nullptr;
+        TD_CUDA(dalloc(c, &d_f, (size_t)(nt - 1) * ns));
+        TD_CUDA(cudaMemcpyAsync(d_f, c->kbar.data(), (size_t)(nt - 1) * ns * sizeof(double),
+                                cudaMemcpyHostToDevice, c->s));
+        TD_CUDA(launch_known_collocation(c, d_f));
+        TD_CUDA(cudaStreamSynchronize(c->s));
+        dfree(c, d_f);
+    }
+    TD_CUDA(dalloc(c, &c->d_b, (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_xa, (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_xb, (size_t)ns));
+    TD_CUDA(cudaMemsetAsync(c->d_b, 0, ns * sizeof(double), c->s));
+    TD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    TD_CUDA(cudaGetLastError());
+    c->prepared = true;
+    c->alpha = 0;
+    c->ms_prepare =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    TD_CUDA(join(c->s, c->user));
+    return TDBEM_OK;
+}
+
+static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_stride)
+{
+    for (int n = 0; n < nsteps; ++n) {
+        int alpha = c->alpha + 1;
+        {
+            PhaseTimer t(c, PH_NEAR);
+            TD_CUDA(launch_near_sum(c, alpha, d_exc ? d_exc + n * exc_stride : nullptr));
+        }
+        c->launches[PH_NEAR] += 1;
+        {
+            PhaseTimer t(c, PH_SOLVE);
+            for (int it = 0; it < c->solve_iters; ++it)
+                TD_CUDA(launch_jacobi(c, alpha, it, it == c->solve_iters - 1));
+        }
+        c->launches[PH_SOLVE] += c->solve_iters;
+        c->alpha = alpha;
+        c->steps_total += 1;
+    }
+    return TDBEM_OK;
+}
+
+int tdbem_step(tdbem_ctx *c, int32_t nsteps)
+{
+    return tdbem_step_io(c, nsteps, nullptr, nullptr, 1);
+}
+
+int tdbem_step_io(tdbem_ctx *c, int32_t nsteps, const double *exc, double *x_out, int32_t on_device)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "step before prepare");
+    if (nsteps < 0 || c->alpha + nsteps > c->P.nt - 1) return fail(c, TDBEM_ERR_ARG, "stepping past Nt-1");
+    if (nsteps == 0) return TDBEM_OK;
+    const int ns = c->ns;
+    TD_CUDA(cudaSetDevice(c->dev));
+    TD_CUDA(join(c->user, c->s));
+    const double *d_exc = exc;
+    if (exc && !on_device) {
+        if (c->exc_cap < nsteps) {
+            dfree(c, c->d_exc);
+            c->d_exc = nullptr;
+            TD_CUDA(dalloc(c, &c->d_exc, (size_t)nsteps * ns));
+            c->exc_cap = nsteps;
+        }
+        TD_CUDA(cudaMemcpyAsync(c->d_exc, exc, (size_t)nsteps * ns * sizeof(double), cudaMemcpyHostToDevice, c->s));
+        d_exc = c->d_exc;
+    }
+    int a0 = c->alpha;
+    int r = step_impl(c, nsteps, d_exc, ns);
+    if (r != TDBEM_OK) return r;
+    if (x_out) {
+        // x^{a-1}: u where phi = 1, q where phi = 0 (Eq. linear)
+        if (on_device) {
+            TD_CUDA(launch_gather_x(c, a0, nsteps, x_out));
+        } else {
+            if (c->xout_cap < nsteps) {
+                dfree(c, c->d_xout);
+                c->d_xout = nullptr;
+                TD_CUDA(dalloc(c, &c->d_xout, (size_t)nsteps * ns));
+                c->xout_cap = nsteps;
+            }
+            TD_CUDA(launch_gather_x(c, a0, nsteps, c->d_xout));
+            TD_CUDA(cudaMemcpyAsync(x_out, c->d_xout, (size_t)nsteps * ns * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->s));
+            TD_CUDA(cudaStreamSynchronize(c->s));
+        }
+    } else if (exc && !on_device) {
+        TD_CUDA(cudaStreamSynchronize(c->s));
+    }
+    TD_CUDA(join(c->s, c->user));
+    return TDBEM_OK;
+}
+
+int tdbem_steps_done(const tdbem_ctx *c, int32_t *out)
+{
+    if (!c || !out) return TDBEM_ERR_ARG;
+    *out = c->alpha;
+    return TDBEM_OK;
+}
+
+int tdbem_get_solution(const tdbem_ctx *cc, double *u, double *q, int32_t beta0, int32_t nbeta, int32_t on_device)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "no solution before prepare");
+    if (beta0 < 0 || nbeta < 0 || beta0 + nbeta > c->P.nt - 1) return fail(c, TDBEM_ERR_ARG, "beta range");
+    size_t n = (size_t)nbeta * c->ns;
+    size_t o = (size_t)beta0 * c->ns;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    TD_CUDA(join(c->user, c->s));
+    if (u) TD_CUDA(cudaMemcpyAsync(u, c->d_u + o, n * sizeof(double), k, c->s));
+    if (q) TD_CUDA(cudaMemcpyAsync(q, c->d_q + o, n * sizeof(double), k, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    return check_flags(c);
+}
+
+int tdbem_get_rhs(const tdbem_ctx *cc, double *b)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !b) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "no rhs before prepare");
+    TD_CUDA(cudaMemcpyAsync(b, c->d_b, c->ns * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    return TDBEM_OK;
+}
+
+int tdbem_get_coefficients(const tdbem_ctx *cc, int32_t kind, const int32_t *rows, int32_t nrows, int32_t gmax,
+                           double *out)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !rows || !out || nrows < 0 || gmax < 0) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "no coefficients before prepare");
+    const double *src = nullptr;
+    if (kind == c->ku_kind) src = c->d_ku;
+    if (kind == c->kw_kind) src = c->d_kw;
+    if (!src) return fail(c, TDBEM_ERR_ARG, "coefficient kind not stored by this run");
+    const int ns = c->ns, nblk = c->nblk;
+    std::vector<uint16_t> meta(ns);
+    std::vector<int64_t> off(nblk);
+    std::vector<int32_t> tot(nblk);
+    std::vector<double> vals;
+    memset(out, 0, sizeof(double) * (size_t)nrows * (gmax + 1) * ns);
+    for (int r = 0; r < nrows; ++r) {
+        int i = rows[r];
+        if (i < 0 || i >= ns) return fail(c, TDBEM_ERR_ARG, "row out of range");
+        TD_CUDA(cudaMemcpyAsync(meta.data(), c->d_meta + (size_t)i * ns, ns * sizeof(uint16_t),
+                                cudaMemcpyDeviceToHost, c->s));
+        TD_CUDA(cudaMemcpyAsync(off.data(), c->d_boff + (size_t)i * nblk, nblk * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, c->s));
+        TD_CUDA(cudaMemcpyAsync(tot.data(), c->d_btot + (size_t)i * nblk, nblk * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, c->s));
+        TD_CUDA(cudaStreamSynchronize(c->s));
+        int64_t first = off[0], last = off[nblk - 1] + tot[nblk - 1];
+        vals.resize((size_t)(last - first));
+        TD_CUDA(cudaMemcpy(vals.data(), src + first, (last - first) * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int b = 0; b < nblk; ++b) {
+            int64_t pos = off[b] - first;
+            int cnt[32], g0[32];
+            for (int l = 0; l < 32; ++l) {
+                int j = b * 32 + l;
+                unsigned m = j < ns ? meta[j] : 0u;
+                cnt[l] = m >> kG0Bits;
+                g0[l] = m & kMaxG0;
+            }
+            for (int s = 0; s < kMaxCnt; ++s)
+                for (int l = 0; l < 32; ++l) {
+                    if (cnt[l] <= s) continue;
+                    int g = g0[l] + s, j = b * 32 + l;
+                    if (g <= gmax) out[((size_t)r * (gmax + 1) + g) * ns + j] = vals[pos];
+                    ++pos;
+                }
+        }
+    }
+    return TDBEM_OK;
+}
+
+int tdbem_get_zero_lag(const tdbem_ctx *cc, double *out)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !out) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "no matrix before prepare");
+    const int ns = c->ns;
+    std::vector<double> aoff((size_t)kEllWidth * ns), ainv(ns);
+    std::vector<int32_t> acol((size_t)kEllWidth * ns);
+    TD_CUDA(cudaMemcpyAsync(aoff.data(), c->d_aoff, aoff.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaMemcpyAsync(acol.data(), c->d_acol, acol.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaMemcpyAsync(ainv.data(), c->d_ainv, ainv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    memset(out, 0, sizeof(double) * (size_t)ns * ns);
+    for (int i = 0; i < ns; ++i) {
+        out[(size_t)i * ns + i] = 1.0 / ainv[i];
+        for (int k = 0; k < kEllWidth; ++k) {
+            int j = acol[(size_t)k * ns + i];
+            if (j >= 0) out[(size_t)i * ns + j] = aoff[(size_t)k * ns + i];
+        }
+    }
+    return TDBEM_OK;
+}
+
+int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !o) return TDBEM_ERR_ARG;
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    harvest(c);
+    memset(o, 0, sizeof(*o));
+    o->ms_rhs = c->ms[PH_RHS];
+    o->ms_near = c->ms[PH_NEAR];
+    o->ms_solve = c->ms[PH_SOLVE];
+    o->ms_total = c->ms[PH_RHS] + c->ms[PH_NEAR] + c->ms[PH_SOLVE];
+    o->launches_rhs = c->launches[PH_RHS];
+    o->launches_near = c->launches[PH_NEAR];
+    o->launches_solve = c->launches[PH_SOLVE];
+    o->steps = c->steps_total;
+    o->n_pairs = c->npairs;
+    o->n_coef = c->ncoef;
+    int kinds = (c->ku_kind >= 0) + (c->kw_kind >= 0);
+    // one full history sum at steady state (every lag of every window in use)
+    o->near_bytes_per_step = c->ncoef * 8 * kinds + c->npairs * 2 + (int64_t)c->ns * c->nblk * 8 +
+                             (int64_t)c->gmax * c->ns * 8 * kinds + (int64_t)c->ns * 8;
+    o->gamma_max = c->gmax;
+    o->solve_iters = c->solve_iters;
+    o->solve_contraction = c->contraction;
+    o->ms_prepare = c->ms_prepare;
+    return TDBEM_OK;
+}
+
+int tdbem_reset_stats(tdbem_ctx *c)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    harvest(c);
+    for (int k = 0; k < PH_COUNT; ++k) {
+        c->ms[k] = 0;
+        c->launches[k] = 0;
+    }
+    c->steps_total = 0;
+    return TDBEM_OK;
+}
+
+int tdbem_sync(tdbem_ctx *c)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    TD_CUDA(cudaGetLastError());
+    return check_flags(c);
+}
+
+}  // extern "C"

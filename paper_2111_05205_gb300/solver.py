@@ -1,0 +1,70 @@
+"""Convenience wrapper: one libtdbem context with numpy in and out.
+
+Only marshals arguments; every computation happens in the CUDA library.
+"""
+
+import numpy as np
+
+from . import abi
+
+
+class Solver:
+    """Time-domain BEM run on the current CUDA device.
+
+    ``xyz`` [nv, 3] vertices, ``tri`` [ns, 3] counter-clockwise triangles,
+    ``c``, ``dt``, ``nt``, ``d`` (B-spline order), ``bie`` ("obie" |
+    "bmbie"), ``phi`` per-element boundary condition (1 Neumann, 0
+    Dirichlet), ``known`` samples of the known data at t_1..t_{nt-1}
+    [(nt-1), ns] or None,
+    ``incident`` (direction, t0, width) of a Gaussian plane pulse or None.
+    ``stream``: a cudaStream_t handle (int) or None.
+    """
+
+    def __init__(self, xyz, tri, c, dt, nt, d, bie, phi=None, known=None, incident=None, stream=None,
+                 solver_tol=0.0, solver_maxit=0):
+        p = abi.tdbem_params()
+        p.c, p.dt, p.nt, p.d = float(c), float(dt), int(nt), int(d)
+        p.bie = {"obie": 0, "bmbie": 1}[bie] if isinstance(bie, str) else int(bie)
+        p.algo = 0
+        p.precision = 0
+        p.solver_tol = float(solver_tol)
+        p.solver_maxit = int(solver_maxit)
+        self.ns = int(np.asarray(tri).shape[0])
+        self.nt = int(nt)
+        self.ctx = abi.tdbem_create(p, stream)
+        try:
+            abi.tdbem_set_mesh(self.ctx, xyz, tri)
+            if phi is not None:
+                abi.tdbem_set_bc(self.ctx, phi)
+            if known is not None:
+                abi.tdbem_set_known(self.ctx, known)
+            if incident is not None:
+                direction, t0, width = incident
+                abi.tdbem_set_incident_plane(self.ctx, direction, t0, width, 0)
+            abi.tdbem_prepare(self.ctx)
+        except Exception:
+            abi.tdbem_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def close(self):
+        if self.ctx is not None:
+            abi.tdbem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=None):
+        n = self.nt - 1 - abi.tdbem_steps_done(self.ctx) if n is None else int(n)
+        abi.tdbem_step(self.ctx, n)
+
+    def solution(self, beta0=0, nbeta=None):
+        nbeta = self.nt - 1 - beta0 if nbeta is None else nbeta
+        return abi.tdbem_get_solution(self.ctx, self.ns, beta0, nbeta)
+
+    def stats(self):
+        return abi.tdbem_get_stats(self.ctx)
