@@ -145,7 +145,7 @@ def run_ours(args):
     t0 = time.time()
     phi = np.full(w.ns, 1 if w.bc == "neumann" else 0, np.int8)
     s = Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi,
-               incident=(w.direction, w.t0, w.sigma), stream=stream)
+               incident=(w.direction, w.t0, w.sigma), stream=stream, precision=args.precision)
     setup_s = time.time() - t0
     st0 = s.stats()
     gmax = st0["gamma_max"]
@@ -161,10 +161,12 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         ev0.record()
         abi.tdbem_step(ctx, args.steps)
         ev1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if dist is not None:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
@@ -217,9 +219,12 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if args.precision == "fp64" else "f64+df32",
         "data": "synthetic",
-        "config": {"workload": args.workload + "_direct_fp64", "ns": w.ns, "d": w.d, "bie": w.bie, "bc": w.bc,
+        "config": {"workload": args.workload + "_direct_" + args.precision, "ns": w.ns,
+                   "precision": ("FP64 coefficients, histories, FMA and solve" if args.precision == "fp64" else
+                                 "FP64 coefficients and solve; history sum on FP32 pairs (48-bit) in "
+                                 "double-float arithmetic"), "d": w.d, "bie": w.bie, "bc": w.bc,
                    "gamma_max": gmax, "spinup_steps": gmax, "coefficients_per_kind": st["n_coef"],
                    "l2": "working set (%.1f GB per step) larger than L2; no flush" %
                          (st["near_bytes_per_step"] / 1e9),
@@ -235,12 +240,42 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     s.close()
+    if args.fp64_form and args.precision != "fp64":
+        out["fp64_form"] = fp64_form(args, w, phi, stream)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, rows=args.cpu_rows)
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def fp64_form(args, w, phi, stream):
+    """The same workload with the FP64 history sum (device steps/s only)."""
+    import torch
+    from paper_2111_05205_gb300 import Solver, abi
+    s = Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi, incident=(w.direction, w.t0, w.sigma),
+               stream=stream, precision="fp64")
+    try:
+        ctx = s.ctx
+        g = s.stats()["gamma_max"]
+        abi.tdbem_step(ctx, g + args.warmup)
+        abi.tdbem_sync(ctx)
+        abi.tdbem_reset_stats(ctx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        abi.tdbem_step(ctx, args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = s.stats()
+        near = st["ms_near"] / max(st["launches_near"], 1)
+        hbm, _ = _peaks()
+        return {"value": 1000.0 / ms, "unit": "time-steps/s", "ms_per_step": ms, "near_avg_ms": near,
+                "near_hbm_frac": st["near_bytes_per_step"] / (near * 1e-3) / 1e9 / hbm}
+    finally:
+        s.close()
 
 
 def _kernel_rev():
@@ -312,6 +347,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="split", choices=["split", "fp64"])
+    ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

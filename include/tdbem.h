@@ -67,9 +67,20 @@ typedef struct {
     int32_t nt;           /* number of time steps Nt >= 2; collocation at t_a, a = 1..Nt-1 */
     int32_t d;            /* B-spline order d, 1 <= d <= 4 (Eq. decompose) */
     int32_t bie;          /* 0 = OBIE (Eq. bie), 1 = BMBIE (Eq. bmbie) */
-    int32_t algo;         /* 0 = direct history sum over all element pairs (Eq. linear) */
-    int32_t precision;    /* 0 = FP64 throughout */
-    int32_t ps, pt, mu, depth; /* space-time FMM parameters; unused by algo 0 */
+    int32_t algo;         /* 0 = direct history sum over all element pairs (Eq. linear);
+                             1 = near pairs (leaf neighbours) direct + the far part by the
+                             interpolation-based space-time FMM (Sections 3-4, Formula 1) */
+    int32_t precision;    /* 0 = FP64 throughout; 1 = split: the history sum stores every
+                             coefficient and history value as an FP32 pair (hi, lo) (48
+                             significant bits) and sums in double-float arithmetic on the
+                             FP32 pipes; coefficients, the zero-lag matrix and the solve
+                             are computed in FP64 either way */
+    int32_t ps, pt;       /* FMM: interpolation points per space / time dimension (2..8,
+                             ps^3 pt <= 1024) */
+    int32_t mu;           /* FMM: near-future intervals (Section 4.2); 0 = the smallest value
+                             for which the kernel is a polynomial over every distant-future
+                             interval (the paper uses 8) */
+    int32_t depth;        /* leaf level L of the spatial hierarchy (root = 0); 0 = none */
     double solver_tol;    /* bound on the zero-lag solve's relative error (0: 1e-16) */
     int32_t solver_maxit; /* cap on zero-lag iterations (0: 200) */
     int32_t reserved;
@@ -91,6 +102,9 @@ typedef struct {
     int32_t solve_iters;           /* zero-lag iterations per step */
     double solve_contraction;      /* max_i sum_{j!=i} |A_ij / A_ii| */
     double ms_prepare;             /* wall time of tdbem_prepare */
+    double ms_far;                 /* FMM: P2M..L2P at leaf-interval boundaries */
+    int64_t launches_far;          /* FMM: boundaries processed */
+    int32_t fmm_lt, fmm_mu;        /* FMM: steps per leaf interval, near-future intervals */
 } tdbem_stats;
 
 /* Creates a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -167,8 +181,44 @@ int tdbem_get_rhs(const tdbem_ctx *ctx, double *b);
 int tdbem_get_coefficients(const tdbem_ctx *ctx, int32_t kind, const int32_t *rows, int32_t nrows,
                            int32_t gmax, double *out);
 
+/* FMM far field of the current leaf interval: out[Lt*ns] host (row t = step
+ * first_step + t), the interpolated far part of the history sum (Eq. target,
+ * Eq. target_m2l; with the Burton-Miller operator for BMBIE).  out may be NULL
+ * to query first_step and nsteps (= Lt).  ERR_STATE without algo 1. */
+int tdbem_get_far(const tdbem_ctx *ctx, double *out, int32_t *first_step, int32_t *nsteps);
+
 /* Zero-lag matrix A of Eq. linear as dense host rows out[ns*ns] (small ns only). */
 int tdbem_get_zero_lag(const tdbem_ctx *ctx, double *out);
+
+/* Spatial hierarchy of the space-time FMM (Section 3, Fig. 2; interaction
+ * lists of Section 4.2, Remark precomp), built by tdbem_prepare when
+ * params.depth = L > 0.  Definition (the paper defers it to its earlier
+ * study): root cube lo = componentwise minimum of the collocation points,
+ * side = largest extent x (1 + 2^-20); element i lies in the leaf cell
+ * floor((x_i - lo) / side * 2^L) (FP64, each operation rounded separately,
+ * clamped to [0, 2^L - 1]); cells are numbered by Morton key (bit b of
+ * x, y, z at 3b, 3b+1, 3b+2) and elements ordered by (leaf key, index); the
+ * occupied cells of level l are the distinct keys >> 3(L - l).  Neighbours
+ * of a cell: occupied cells within one cell in every axis (itself
+ * included); interaction list (levels >= 2): occupied children of the
+ * parent's neighbours that are not neighbours (at most 189).  Lists are
+ * ordered by key and given as cell indices of the level.
+ * what: TDBEM_TREE_BOX (double[4]: lo, side; level ignored), _PERM (int32
+ * [ns]: element at each sorted position), _KEYS (uint64 [ncells]), _START
+ * (int32 [ncells+1]: first sorted position of each cell), _NBR_OFF /
+ * _IL_OFF (int32 [ncells+1] CSR offsets), _NBR / _IL (int32 entries),
+ * _NEAR_OFF (int64 [ns+1], algo 1: row offsets in element numbering) and
+ * _NEAR (int32: for each element, every element of the leaf cells that
+ * neighbour its own, cells by key and elements in sorted order).
+ * *count receives the number of entries; out may be NULL to query it;
+ * otherwise out is a host buffer of that many entries.  ERR_STATE without a
+ * hierarchy. */
+enum {
+    TDBEM_TREE_BOX = 0, TDBEM_TREE_PERM = 1, TDBEM_TREE_KEYS = 2, TDBEM_TREE_START = 3,
+    TDBEM_TREE_NBR_OFF = 4, TDBEM_TREE_NBR = 5, TDBEM_TREE_IL_OFF = 6, TDBEM_TREE_IL = 7,
+    TDBEM_TREE_NEAR_OFF = 8, TDBEM_TREE_NEAR = 9
+};
+int tdbem_get_tree(const tdbem_ctx *ctx, int32_t what, int32_t level, void *out, int64_t *count);
 
 int tdbem_get_stats(const tdbem_ctx *ctx, tdbem_stats *out);
 int tdbem_reset_stats(tdbem_ctx *ctx);

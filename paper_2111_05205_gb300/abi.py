@@ -38,7 +38,9 @@ class tdbem_stats(ctypes.Structure):
                 ("launches_near", ctypes.c_int64), ("launches_solve", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64), ("n_coef", ctypes.c_int64), ("near_bytes_per_step", ctypes.c_int64),
                 ("gamma_max", ctypes.c_int32), ("solve_iters", ctypes.c_int32),
-                ("solve_contraction", ctypes.c_double), ("ms_prepare", ctypes.c_double)]
+                ("solve_contraction", ctypes.c_double), ("ms_prepare", ctypes.c_double),
+                ("ms_far", ctypes.c_double), ("launches_far", ctypes.c_int64), ("fmm_lt", ctypes.c_int32),
+                ("fmm_mu", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -64,6 +66,8 @@ SIGNATURES = {
     "tdbem_get_rhs": (ctypes.c_int, [_P, _P]),
     "tdbem_get_coefficients": (ctypes.c_int, [_P, _I, _P, _I, _I, _P]),
     "tdbem_get_zero_lag": (ctypes.c_int, [_P, _P]),
+    "tdbem_get_far": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "tdbem_get_tree": (ctypes.c_int, [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_int64)]),
     "tdbem_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(tdbem_stats)]),
     "tdbem_reset_stats": (ctypes.c_int, [_P]),
     "tdbem_sync": (ctypes.c_int, [_P]),
@@ -182,9 +186,34 @@ def tdbem_get_coefficients(ctx, kind, rows, gmax, ns):
     return out
 
 
+def tdbem_get_far(ctx, ns):
+    """(far [Lt, ns], first step) of the current leaf interval (FMM)."""
+    a0, n = _I(), _I()
+    _check(ctx, lib().tdbem_get_far(ctx, None, ctypes.byref(a0), ctypes.byref(n)))
+    out = np.zeros((n.value, ns))
+    _check(ctx, lib().tdbem_get_far(ctx, _ptr(out), ctypes.byref(a0), ctypes.byref(n)))
+    return out, a0.value
+
+
 def tdbem_get_zero_lag(ctx, ns):
     out = np.zeros((ns, ns))
     _check(ctx, lib().tdbem_get_zero_lag(ctx, _ptr(out)))
+    return out
+
+
+TREE = {"box": (0, np.float64), "perm": (1, np.int32), "keys": (2, np.uint64), "start": (3, np.int32),
+        "nbr_off": (4, np.int32), "nbr": (5, np.int32), "il_off": (6, np.int32), "il": (7, np.int32),
+        "near_off": (8, np.int64), "near": (9, np.int32)}
+
+
+def tdbem_get_tree(ctx, what, level=0):
+    """One item of the hierarchy as a numpy array (see include/tdbem.h)."""
+    code, dt = TREE[what]
+    n = ctypes.c_int64()
+    _check(ctx, lib().tdbem_get_tree(ctx, code, int(level), None, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=dt)
+    if n.value:
+        _check(ctx, lib().tdbem_get_tree(ctx, code, int(level), _ptr(out), ctypes.byref(n)))
     return out
 
 
@@ -200,3 +229,4 @@ def tdbem_reset_stats(ctx):
 
 def tdbem_sync(ctx):
     _check(ctx, lib().tdbem_sync(ctx))
+

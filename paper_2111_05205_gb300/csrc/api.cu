@@ -122,11 +122,12 @@ int tdbem_create(const tdbem_params *p, void *stream, tdbem_ctx **out)
     if (!p || !out) return TDBEM_ERR_ARG;
     *out = nullptr;
     if (!(p->c > 0) || !(p->dt > 0) || p->nt < 2 || p->d < 1 || p->d > kMaxD || (p->bie != 0 && p->bie != 1) ||
-        p->algo != 0 || p->precision != 0)
+        (p->algo != 0 && p->algo != 1) || (p->precision != 0 && p->precision != 1))
         return TDBEM_ERR_ARG;
     c = new tdbem_ctx();
     c->P = *p;
     c->cdt = p->c * p->dt;
+    c->split = (p->precision == 1);
     c->user = (cudaStream_t)stream;
     cudaGetDevice(&c->dev);
     if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -154,6 +155,7 @@ void tdbem_destroy(tdbem_ctx *c)
     harvest(c);
     for (auto e : c->pool) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
+    free_tree(c);
     if (c->s) cudaStreamDestroy(c->s);
     delete c;
 }
@@ -262,9 +264,49 @@ int tdbem_prepare(tdbem_ctx *c)
     TD_CUDA(cudaMemcpyAsync(c->d_phi, c->phi.data(), ns, cudaMemcpyHostToDevice, c->s));
     TD_CUDA(launch_geometry(c));
 
-    // lag windows of all pairs
-    c->nblk = (ns + 31) / 32;
-    TD_CUDA(dalloc(c, &c->d_meta, (size_t)ns * ns));
+    // spatial hierarchy of the FMM (also built for the direct path when a
+    // depth is given, for inspection)
+    if (c->P.algo == 1 && c->P.depth < 2) return fail(c, TDBEM_ERR_ARG, "the FMM needs depth >= 2");
+    if (c->P.depth > 0) {
+        if (c->P.depth > 10) return fail(c, TDBEM_ERR_ARG, "depth above 10");
+        TD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->s));
+        std::string why;
+        TD_CUDA(build_tree(c, why));
+        if (!why.empty()) return fail(c, TDBEM_ERR_ARG, why);
+    }
+    if (c->P.algo == 1) {
+        std::string why;
+        TD_CUDA(fmm_setup(c, why));
+        if (!why.empty())
+            return fail(c, why.find("infeasible") != std::string::npos ? TDBEM_ERR_INFEASIBLE_HIERARCHY : TDBEM_ERR_ARG,
+                        why);
+    }
+
+    // pair lists: every pair (direct path) or the near pairs of the leaf
+    // neighbour cells (FMM path)
+    if (c->P.algo == 1) {
+        TD_CUDA(build_near_lists(c));
+    } else {
+        std::vector<int64_t> prow(ns + 1), rowblk(ns + 1);
+        const int64_t nbr = (ns + 31) / 32;
+        for (int i = 0; i <= ns; ++i) {
+            prow[i] = (int64_t)i * ns;
+            rowblk[i] = (int64_t)i * nbr;
+        }
+        TD_CUDA(dalloc(c, &c->d_prow, (size_t)ns + 1));
+        TD_CUDA(dalloc(c, &c->d_rowblk, (size_t)ns + 1));
+        TD_CUDA(cudaMemcpyAsync(c->d_prow, prow.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+        TD_CUDA(cudaMemcpyAsync(c->d_rowblk, rowblk.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                c->s));
+        TD_CUDA(cudaStreamSynchronize(c->s));
+        c->npairs = (int64_t)ns * ns;
+        c->nbt = (int64_t)ns * nbr;
+    }
+
+    // lag windows of the pairs and coefficients per 32-pair block
+    TD_CUDA(dalloc(c, &c->d_meta, (size_t)c->npairs));
+    TD_CUDA(dalloc(c, &c->d_btot, (size_t)c->nbt));
+    TD_CUDA(dalloc(c, &c->d_boff, (size_t)c->nbt));
     int *d_m = c->d_flag + 1;  // flag[1..3]: max cnt, max g0, max lag
     TD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->s));
     TD_CUDA(launch_windows(c, d_m, d_m + 1, d_m + 2));
@@ -273,51 +315,59 @@ int tdbem_prepare(tdbem_ctx *c)
     TD_CUDA(cudaStreamSynchronize(c->s));
     if (mx[0] > kMaxCnt) return fail(c, TDBEM_ERR_ARG, "lag window longer than 15 (element larger than ~10 c*dt)");
     if (mx[1] > kMaxG0) return fail(c, TDBEM_ERR_ARG, "lag beyond 4095 (surface too large for c*dt)");
-    c->smax = mx[0];
+    c->smax = std::max(mx[0], 1);
     c->gmax = mx[2];
 
-    // packed coefficient layout: per 32-pair block totals, prefix on the host
-    size_t nb = (size_t)ns * c->nblk;
-    TD_CUDA(dalloc(c, &c->d_btot, nb));
-    TD_CUDA(dalloc(c, &c->d_boff, nb));
-    TD_CUDA(launch_block_totals(c));
-    std::vector<int32_t> tot(nb);
-    std::vector<int64_t> off(nb);
-    TD_CUDA(cudaMemcpyAsync(tot.data(), c->d_btot, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
-    TD_CUDA(cudaStreamSynchronize(c->s));
-    int64_t run = 0;
-    for (size_t k = 0; k < nb; ++k) {
-        off[k] = run;
-        run += tot[k];
+    // packed coefficient layout: block offsets by a prefix on the host
+    {
+        size_t nb = (size_t)c->nbt;
+        std::vector<int32_t> tot(nb);
+        std::vector<int64_t> off(nb);
+        TD_CUDA(cudaMemcpyAsync(tot.data(), c->d_btot, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+        TD_CUDA(cudaStreamSynchronize(c->s));
+        int64_t run = 0;
+        for (size_t k = 0; k < nb; ++k) {
+            off[k] = run;
+            run += tot[k];
+        }
+        c->ncoef = run;
+        TD_CUDA(cudaMemcpyAsync(c->d_boff, off.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+        TD_CUDA(cudaStreamSynchronize(c->s));
     }
-    c->ncoef = run;
-    c->npairs = (int64_t)ns * ns;
-    TD_CUDA(cudaMemcpyAsync(c->d_boff, off.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
 
     // influence coefficients
     if (c->ku_kind >= 0) TD_CUDA(dalloc(c, &c->d_ku, (size_t)c->ncoef));
     if (c->kw_kind >= 0) TD_CUDA(dalloc(c, &c->d_kw, (size_t)c->ncoef));
     TD_CUDA(launch_coefficients(c));
 
-    // zero-lag matrix and its Jacobi contraction factor
-    TD_CUDA(dalloc(c, &c->d_aoff, (size_t)kEllWidth * ns));
-    TD_CUDA(dalloc(c, &c->d_acol, (size_t)kEllWidth * ns));
+    // zero-lag matrix (width of its ELL store counted first) and the Jacobi
+    // contraction factor
+    TD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->s));
     TD_CUDA(dalloc(c, &c->d_ainv, (size_t)ns));
-    TD_CUDA(launch_zero_lag(c));
-    std::vector<double> aoff((size_t)kEllWidth * ns), ainv(ns);
-    std::vector<int32_t> acol((size_t)kEllWidth * ns);
+    TD_CUDA(launch_zero_lag(c, true));
+    int cnt_w = 0;
+    TD_CUDA(cudaMemcpyAsync(&cnt_w, c->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    c->ell_w = std::max(cnt_w, 1);
+    const int W = c->ell_w;
+    TD_CUDA(dalloc(c, &c->d_aoff, (size_t)W * ns));
+    TD_CUDA(dalloc(c, &c->d_acol, (size_t)W * ns));
+    TD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->s));
+    TD_CUDA(launch_zero_lag(c, false));
+    std::vector<double> aoff((size_t)W * ns), ainv(ns);
+    std::vector<int32_t> acol((size_t)W * ns);
     int fl = 0;
     TD_CUDA(cudaMemcpyAsync(aoff.data(), c->d_aoff, aoff.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     TD_CUDA(cudaMemcpyAsync(acol.data(), c->d_acol, acol.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
     TD_CUDA(cudaMemcpyAsync(ainv.data(), c->d_ainv, ainv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     TD_CUDA(cudaMemcpyAsync(&fl, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     TD_CUDA(cudaStreamSynchronize(c->s));
-    if (fl & 2) return fail(c, TDBEM_ERR_ARG, "zero-lag row with more than 8 off-diagonal entries");
+    if (fl & 2) return fail(c, TDBEM_ERR_ARG, "zero-lag row wider than its counted width");
     if (fl & 4) return fail(c, TDBEM_ERR_ARG, "zero-lag matrix has a zero diagonal entry");
     double qmax = 0.0;
     for (int i = 0; i < ns; ++i) {
         double s = 0.0;
-        for (int k = 0; k < kEllWidth; ++k)
+        for (int k = 0; k < W; ++k)
             if (acol[(size_t)k * ns + i] >= 0) s += fabs(aoff[(size_t)k * ns + i]);
         qmax = std::max(qmax, s * fabs(ainv[i]));
     }
@@ -348,6 +398,12 @@ int tdbem_prepare(tdbem_ctx *c)
         TD_CUDA(cudaStreamSynchronize(c->s));
         dfree(c, d_f);
     }
+    if (c->split) {
+        TD_CUDA(dalloc(c, &c->d_us, nh));
+        TD_CUDA(dalloc(c, &c->d_qs, nh));
+        TD_CUDA(launch_split_histories(c));
+        TD_CUDA(launch_split_coefficients(c));
+    }
     TD_CUDA(dalloc(c, &c->d_b, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xa, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xb, (size_t)ns));
@@ -367,9 +423,23 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
 {
     for (int n = 0; n < nsteps; ++n) {
         int alpha = c->alpha + 1;
+        const double *far = nullptr;
+        if (c->fmm.on) {
+            // far field of the leaf interval that holds step alpha (Section 3)
+            int kobs = (alpha - 1) / c->fmm.Lt;
+            if (kobs != c->fmm.far_k) {
+                if (kobs > 0) {
+                    PhaseTimer t(c, PH_FAR);
+                    TD_CUDA(fmm_boundary(c, kobs - 1));
+                    c->launches[PH_FAR] += 1;
+                }
+                c->fmm.far_k = kobs;
+            }
+            far = c->fmm.far + (size_t)(alpha - 1 - kobs * c->fmm.Lt) * c->ns;
+        }
         {
             PhaseTimer t(c, PH_NEAR);
-            TD_CUDA(launch_near_sum(c, alpha, d_exc ? d_exc + n * exc_stride : nullptr));
+            TD_CUDA(launch_near_sum(c, alpha, d_exc ? d_exc + n * exc_stride : nullptr, far));
         }
         c->launches[PH_NEAR] += 1;
         {
@@ -478,42 +548,71 @@ int tdbem_get_coefficients(const tdbem_ctx *cc, int32_t kind, const int32_t *row
     if (kind == c->ku_kind) src = c->d_ku;
     if (kind == c->kw_kind) src = c->d_kw;
     if (!src) return fail(c, TDBEM_ERR_ARG, "coefficient kind not stored by this run");
-    const int ns = c->ns, nblk = c->nblk;
-    std::vector<uint16_t> meta(ns);
-    std::vector<int64_t> off(nblk);
-    std::vector<int32_t> tot(nblk);
-    std::vector<double> vals;
+    const int ns = c->ns;
     memset(out, 0, sizeof(double) * (size_t)nrows * (gmax + 1) * ns);
+    std::vector<int64_t> prow(ns + 1), rowblk(ns + 1);
+    TD_CUDA(cudaMemcpy(prow.data(), c->d_prow, (ns + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    TD_CUDA(cudaMemcpy(rowblk.data(), c->d_rowblk, (ns + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    std::vector<uint16_t> meta;
+    std::vector<int32_t> cols, tot;
+    std::vector<int64_t> off;
+    std::vector<double> vals;
     for (int r = 0; r < nrows; ++r) {
         int i = rows[r];
         if (i < 0 || i >= ns) return fail(c, TDBEM_ERR_ARG, "row out of range");
-        TD_CUDA(cudaMemcpyAsync(meta.data(), c->d_meta + (size_t)i * ns, ns * sizeof(uint16_t),
-                                cudaMemcpyDeviceToHost, c->s));
-        TD_CUDA(cudaMemcpyAsync(off.data(), c->d_boff + (size_t)i * nblk, nblk * sizeof(int64_t),
-                                cudaMemcpyDeviceToHost, c->s));
-        TD_CUDA(cudaMemcpyAsync(tot.data(), c->d_btot + (size_t)i * nblk, nblk * sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, c->s));
-        TD_CUDA(cudaStreamSynchronize(c->s));
-        int64_t first = off[0], last = off[nblk - 1] + tot[nblk - 1];
+        int64_t np = prow[i + 1] - prow[i], nb = rowblk[i + 1] - rowblk[i];
+        meta.resize(np);
+        cols.resize(np);
+        off.resize(nb);
+        tot.resize(nb);
+        if (np == 0) continue;
+        TD_CUDA(cudaMemcpy(meta.data(), c->d_meta + prow[i], np * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+        if (c->d_col) TD_CUDA(cudaMemcpy(cols.data(), c->d_col + prow[i], np * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        TD_CUDA(cudaMemcpy(off.data(), c->d_boff + rowblk[i], nb * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        TD_CUDA(cudaMemcpy(tot.data(), c->d_btot + rowblk[i], nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        int64_t first = off[0], last = off[nb - 1] + tot[nb - 1];
         vals.resize((size_t)(last - first));
-        TD_CUDA(cudaMemcpy(vals.data(), src + first, (last - first) * sizeof(double), cudaMemcpyDeviceToHost));
-        for (int b = 0; b < nblk; ++b) {
+        if (last > first)
+            TD_CUDA(cudaMemcpy(vals.data(), src + first, (last - first) * sizeof(double), cudaMemcpyDeviceToHost));
+        if (c->split)
+            for (auto &v : vals) {
+                float hl[2];
+                memcpy(hl, &v, sizeof(hl));
+                v = (double)hl[0] + (double)hl[1];
+            }
+        for (int64_t b = 0; b < nb; ++b) {
             int64_t pos = off[b] - first;
-            int cnt[32], g0[32];
+            int cnt[32], g0[32], jj[32];
             for (int l = 0; l < 32; ++l) {
-                int j = b * 32 + l;
-                unsigned m = j < ns ? meta[j] : 0u;
+                int64_t pr = b * 32 + l;
+                unsigned m = pr < np ? meta[pr] : 0u;
                 cnt[l] = m >> kG0Bits;
                 g0[l] = m & kMaxG0;
+                jj[l] = pr < np ? (c->d_col ? cols[pr] : (int)pr) : 0;
             }
             for (int s = 0; s < kMaxCnt; ++s)
                 for (int l = 0; l < 32; ++l) {
                     if (cnt[l] <= s) continue;
-                    int g = g0[l] + s, j = b * 32 + l;
-                    if (g <= gmax) out[((size_t)r * (gmax + 1) + g) * ns + j] = vals[pos];
+                    int g = g0[l] + s;
+                    if (g <= gmax) out[((size_t)r * (gmax + 1) + g) * ns + jj[l]] = vals[pos];
                     ++pos;
                 }
         }
+    }
+    return TDBEM_OK;
+}
+
+int tdbem_get_far(const tdbem_ctx *cc, double *out, int32_t *first_step, int32_t *nsteps)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !first_step || !nsteps) return TDBEM_ERR_ARG;
+    if (!c->prepared || !c->fmm.on) return fail(c, TDBEM_ERR_STATE, "no far field (algo 0 or not prepared)");
+    const int k = std::max(c->fmm.far_k, 0);
+    *first_step = k * c->fmm.Lt + 1;
+    *nsteps = c->fmm.Lt;
+    if (out) {
+        TD_CUDA(cudaStreamSynchronize(c->s));
+        TD_CUDA(cudaMemcpy(out, c->fmm.far, (size_t)c->fmm.Lt * c->ns * sizeof(double), cudaMemcpyDeviceToHost));
     }
     return TDBEM_OK;
 }
@@ -524,8 +623,9 @@ int tdbem_get_zero_lag(const tdbem_ctx *cc, double *out)
     if (!c || !out) return TDBEM_ERR_ARG;
     if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "no matrix before prepare");
     const int ns = c->ns;
-    std::vector<double> aoff((size_t)kEllWidth * ns), ainv(ns);
-    std::vector<int32_t> acol((size_t)kEllWidth * ns);
+    const int W = c->ell_w;
+    std::vector<double> aoff((size_t)W * ns), ainv(ns);
+    std::vector<int32_t> acol((size_t)W * ns);
     TD_CUDA(cudaMemcpyAsync(aoff.data(), c->d_aoff, aoff.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     TD_CUDA(cudaMemcpyAsync(acol.data(), c->d_acol, acol.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
     TD_CUDA(cudaMemcpyAsync(ainv.data(), c->d_ainv, ainv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
@@ -533,12 +633,85 @@ int tdbem_get_zero_lag(const tdbem_ctx *cc, double *out)
     memset(out, 0, sizeof(double) * (size_t)ns * ns);
     for (int i = 0; i < ns; ++i) {
         out[(size_t)i * ns + i] = 1.0 / ainv[i];
-        for (int k = 0; k < kEllWidth; ++k) {
+        for (int k = 0; k < W; ++k) {
             int j = acol[(size_t)k * ns + i];
             if (j >= 0) out[(size_t)i * ns + j] = aoff[(size_t)k * ns + i];
         }
     }
     return TDBEM_OK;
+}
+
+int tdbem_get_tree(const tdbem_ctx *cc, int32_t what, int32_t level, void *out, int64_t *count)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !count) return TDBEM_ERR_ARG;
+    if (!c->prepared || c->tree.levels.empty()) return fail(c, TDBEM_ERR_STATE, "no hierarchy (depth 0)");
+    const int ns = c->ns;
+    if (what == TDBEM_TREE_BOX) {
+        *count = 4;
+        if (out) TD_CUDA(cudaMemcpy(out, c->tree.box, 4 * sizeof(double), cudaMemcpyDeviceToHost));
+        return TDBEM_OK;
+    }
+    if (what == TDBEM_TREE_PERM) {
+        *count = ns;
+        if (out) TD_CUDA(cudaMemcpy(out, c->tree.perm, ns * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        return TDBEM_OK;
+    }
+    if (what == TDBEM_TREE_NEAR_OFF || what == TDBEM_TREE_NEAR) {
+        if (!c->d_col) return fail(c, TDBEM_ERR_STATE, "no near lists (algo 0)");
+        if (what == TDBEM_TREE_NEAR_OFF) {
+            *count = ns + 1;
+            if (out) {
+                std::vector<int64_t> pr(ns + 1);
+                TD_CUDA(cudaMemcpy(pr.data(), c->d_prow, (ns + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+                for (int i = 0; i <= ns; ++i) ((int64_t *)out)[i] = pr[i];
+            }
+        } else {
+            *count = c->npairs;
+            if (out) TD_CUDA(cudaMemcpy(out, c->d_col, c->npairs * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        return TDBEM_OK;
+    }
+    if (level < 0 || level >= (int)c->tree.levels.size()) return fail(c, TDBEM_ERR_ARG, "level out of range");
+    const TreeLevel &T = c->tree.levels[level];
+    const int nc = T.nc;
+    auto csr = [&](const int32_t *dlist, const int32_t *dcount, int stride, bool offsets) -> int {
+        std::vector<int32_t> cnt(nc), lst((size_t)nc * stride);
+        if (dcount) {
+            TD_CUDA(cudaMemcpy(cnt.data(), dcount, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            TD_CUDA(cudaMemcpy(lst.data(), dlist, lst.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        int64_t tot = 0;
+        for (int k = 0; k < nc; ++k) tot += cnt[k];
+        *count = offsets ? nc + 1 : tot;
+        if (!out) return TDBEM_OK;
+        int32_t *o = (int32_t *)out;
+        int64_t run = 0;
+        for (int k = 0; k < nc; ++k) {
+            if (offsets)
+                o[k] = (int32_t)run;
+            else
+                for (int a = 0; a < cnt[k]; ++a) o[run + a] = lst[(size_t)k * stride + a];
+            run += cnt[k];
+        }
+        if (offsets) o[nc] = (int32_t)run;
+        return TDBEM_OK;
+    };
+    switch (what) {
+    case TDBEM_TREE_KEYS:
+        *count = nc;
+        if (out) TD_CUDA(cudaMemcpy(out, T.ckey, nc * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        return TDBEM_OK;
+    case TDBEM_TREE_START:
+        *count = nc + 1;
+        if (out) TD_CUDA(cudaMemcpy(out, T.cstart, (nc + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        return TDBEM_OK;
+    case TDBEM_TREE_NBR_OFF: return csr(T.nbr, T.ncount, 27, true);
+    case TDBEM_TREE_NBR: return csr(T.nbr, T.ncount, 27, false);
+    case TDBEM_TREE_IL_OFF: return csr(T.il, T.ilcount, 189, true);
+    case TDBEM_TREE_IL: return csr(T.il, T.ilcount, 189, false);
+    default: return fail(c, TDBEM_ERR_ARG, "unknown tree item");
+    }
 }
 
 int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
@@ -551,7 +724,11 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->ms_rhs = c->ms[PH_RHS];
     o->ms_near = c->ms[PH_NEAR];
     o->ms_solve = c->ms[PH_SOLVE];
-    o->ms_total = c->ms[PH_RHS] + c->ms[PH_NEAR] + c->ms[PH_SOLVE];
+    o->ms_far = c->ms[PH_FAR];
+    o->launches_far = c->launches[PH_FAR];
+    o->fmm_lt = c->fmm.Lt;
+    o->fmm_mu = c->fmm.mu;
+    o->ms_total = c->ms[PH_RHS] + c->ms[PH_NEAR] + c->ms[PH_SOLVE] + c->ms[PH_FAR];
     o->launches_rhs = c->launches[PH_RHS];
     o->launches_near = c->launches[PH_NEAR];
     o->launches_solve = c->launches[PH_SOLVE];
@@ -560,7 +737,7 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->n_coef = c->ncoef;
     int kinds = (c->ku_kind >= 0) + (c->kw_kind >= 0);
     // one full history sum at steady state (every lag of every window in use)
-    o->near_bytes_per_step = c->ncoef * 8 * kinds + c->npairs * 2 + (int64_t)c->ns * c->nblk * 8 +
+    o->near_bytes_per_step = c->ncoef * 8 * kinds + c->npairs * (c->d_col ? 6 : 2) + c->nbt * 8 +
                              (int64_t)c->gmax * c->ns * 8 * kinds + (int64_t)c->ns * 8;
     o->gamma_max = c->gmax;
     o->solve_iters = c->solve_iters;

@@ -5,6 +5,7 @@
 namespace tdbem {
 
 constexpr int kNearThreads = 128;
+constexpr int kUnroll = 4;  // window slots whose loads are issued together
 
 // Incident-wave term e_i(t_a) of the total-field equation: u_in (OBIE) or
 // (d/dn_x - c^-1 d/dt) u_in (BMBIE) for the plane pulse
@@ -22,49 +23,163 @@ __device__ __forceinline__ double incident_term(const Incident &in, const double
     return -(1.0 + kn) / in.c * df;
 }
 
+// Double-float helpers of the split-precision history sum: a value v is
+// held as (hi, lo) = (fl32(v), fl32(v - hi)), 48 significant bits; the
+// product of two such values is formed exactly in its leading part
+// (hi*hi and its FMA residual) plus the two cross terms, and added to a
+// (hi, lo) accumulator by the two-sum of Knuth.  Relative error of one
+// product ~2^-47, so the FP32 pipes (57x the FP64 rate on this GPU) carry
+// an FP64-grade sum.
+struct DF {
+    float h, l;
+};
+
+__device__ __forceinline__ void df_fma(DF &acc, float ch, float cl, float xh, float xl)
+{
+    float ph = ch * xh;
+    float pe = fmaf(ch, xh, -ph);
+    pe = fmaf(ch, xl, pe);
+    pe = fmaf(cl, xh, pe);
+    float s = acc.h + ph;
+    float bb = s - acc.h;
+    float err = (acc.h - (s - bb)) + (ph - bb);
+    acc.l += err + pe;
+    acc.h = s;
+}
+
+__device__ __forceinline__ void df_renorm(DF &a)
+{
+    float s = a.h + a.l;
+    a.l = a.l - (s - a.h);
+    a.h = s;
+}
+
 // b_i = -e_i - sum_j sum_{g in window(i,j), g <= a} (KU^(g)_ij q_j^{a-g} - KW^(g)_ij u_j^{a-g})
 // One CTA per row i; each warp walks 32-pair blocks of the row.  Window
 // slot s of a block is stored packed (lanes with cnt > s, in lane order),
 // so every load of the coefficient stream is a contiguous warp access; the
 // history entries x_j^{a-g} of one slot differ only by the lanes' g0.
 // The row sum is reduced in a fixed order (deterministic).
-__global__ void __launch_bounds__(kNearThreads) k_near_sum(int ns, int nblk, int alpha,
+// SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
+// coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
+// are read from their float-pair copies and the sum runs in double-float.
+template <bool HU, bool HW, bool SPLIT>
+__global__ void __launch_bounds__(kNearThreads) k_near_sum(int ns, int alpha, const int64_t *__restrict__ prow,
+                                                           const int32_t *__restrict__ col,
+                                                           const int64_t *__restrict__ rowblk,
                                                            const uint16_t *__restrict__ meta,
                                                            const int64_t *__restrict__ boff,
                                                            const double *__restrict__ ku,
                                                            const double *__restrict__ kw,
-                                                           const double *__restrict__ u,
+                                                           const double *__restrict__ u_,
                                                            const double *__restrict__ q,
+                                                           const float2 *__restrict__ us,
+                                                           const float2 *__restrict__ qs,
                                                            const double *__restrict__ exc, Incident inc,
                                                            const double *__restrict__ xc,
-                                                           const double *__restrict__ nrm, double *b)
+                                                           const double *__restrict__ nrm,
+                                                           const double *__restrict__ far, double *b)
 {
     __shared__ double red[kNearThreads / 32];
     const int i = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const uint16_t *mrow = meta + (int64_t)i * ns;
-    const int64_t *orow = boff + (int64_t)i * nblk;
+    const int64_t p0 = prow[i];
+    const int npr = (int)(prow[i + 1] - p0);
+    const uint16_t *mrow = meta + p0;
+    const int32_t *crow = col ? col + p0 : nullptr;
+    const int64_t *orow = boff + rowblk[i];
+    const int nblk = (int)(rowblk[i + 1] - rowblk[i]);
     double acc = 0.0;
-    for (int bk = warp; bk < nblk; bk += kNearThreads / 32) {
-        int j = bk * 32 + lane;
-        unsigned m = (j < ns) ? mrow[j] : 0u;
-        int g0 = m & kMaxG0, cnt = m >> kG0Bits;
-        int64_t pos = orow[bk];
-        int sm = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
-        // lag g = g0 + s reaches back to beta = alpha - g
-        int beta = alpha - g0;
-        for (int s = 0; s < sm; ++s, --beta) {
-            unsigned mask = __ballot_sync(0xffffffffu, cnt > s);
-            if (cnt > s && beta >= 0) {
-                int64_t idx = pos + __popc(mask & lt);
-                int64_t h = (int64_t)beta * ns + j;
-                if (ku) acc -= ku[idx] * q[h];
-                if (kw) acc += kw[idx] * u[h];
-            }
-            pos += __popc(mask);
-        }
+    DF dacc = {0.f, 0.f};
+    // metadata of the first block; the next block's is fetched while the
+    // current one is summed
+    int bk = warp;
+    unsigned mnext = 0u;
+    int64_t onext = 0;
+    if (bk < nblk) {
+        int pr = bk * 32 + lane;
+        mnext = (pr < npr) ? mrow[pr] : 0u;
+        onext = orow[bk];
     }
+    for (; bk < nblk; bk += kNearThreads / 32) {
+        const int pr = bk * 32 + lane;
+        const int j = (pr < npr) ? (crow ? crow[pr] : pr) : 0;
+        const unsigned m = mnext;
+        int64_t pos = onext;
+        int nb = bk + kNearThreads / 32;
+        if (nb < nblk) {
+            int pn = nb * 32 + lane;
+            mnext = (pn < npr) ? mrow[pn] : 0u;
+            onext = orow[nb];
+        }
+        const int g0 = m & kMaxG0, cnt = m >> kG0Bits;  // cnt = 0 past the row's end
+        const int sm = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+        // lag g = g0 + s reaches back to beta = alpha - g
+        const int beta0 = alpha - g0;
+        const int64_t h0 = (int64_t)beta0 * ns + j;
+        // groups of kUnroll window slots: every load of a group is issued
+        // before any of them is used
+        for (int s0 = 0; s0 < sm; s0 += kUnroll) {
+            int64_t idx[kUnroll];
+            bool act[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                int s = s0 + u;
+                unsigned mask = __ballot_sync(0xffffffffu, cnt > s);
+                act[u] = cnt > s && beta0 - s >= 0;
+                idx[u] = pos + __popc(mask & lt);
+                pos += __popc(mask);
+            }
+            if (SPLIT) {
+                float2 cu[kUnroll], xu[kUnroll], cw[kUnroll], xw[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    int64_t h = h0 - (int64_t)(s0 + u) * ns;
+                    if (act[u]) {
+                        if (HU) {
+                            cu[u] = __ldcs(reinterpret_cast<const float2 *>(ku) + idx[u]);
+                            xu[u] = qs[h];
+                        }
+                        if (HW) {
+                            cw[u] = __ldcs(reinterpret_cast<const float2 *>(kw) + idx[u]);
+                            xw[u] = us[h];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+                    if (act[u]) {
+                        if (HU) df_fma(dacc, -cu[u].x, -cu[u].y, xu[u].x, xu[u].y);
+                        if (HW) df_fma(dacc, cw[u].x, cw[u].y, xw[u].x, xw[u].y);
+                    }
+            } else {
+                double cu[kUnroll], xu[kUnroll], cw[kUnroll], xw[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    int64_t h = h0 - (int64_t)(s0 + u) * ns;
+                    if (act[u]) {
+                        if (HU) {
+                            cu[u] = __ldcs(ku + idx[u]);
+                            xu[u] = q[h];
+                        }
+                        if (HW) {
+                            cw[u] = __ldcs(kw + idx[u]);
+                            xw[u] = u_[h];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+                    if (act[u]) {
+                        if (HU) acc -= cu[u] * xu[u];
+                        if (HW) acc += cw[u] * xw[u];
+                    }
+            }
+        }
+        if (SPLIT) df_renorm(dacc);
+    }
+    if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
@@ -76,14 +191,62 @@ __global__ void __launch_bounds__(kNearThreads) k_near_sum(int ns, int nblk, int
             e = exc[i];
         else if (inc.on)
             e = incident_term(inc, xc + 3 * i, nrm + 3 * i, alpha);
+        if (far) e += far[i];
         b[i] = t - e;
     }
 }
 
-cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc)
+template <bool SPLIT>
+static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
-    k_near_sum<<<c->ns, kNearThreads, 0, c->s>>>(c->ns, c->nblk, alpha, c->d_meta, c->d_boff, c->d_ku, c->d_kw,
-                                                c->d_u, c->d_q, d_exc, c->inc, c->d_xc, c->d_n, c->d_b);
+    bool hu = c->d_ku != nullptr, hw = c->d_kw != nullptr;
+    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT> : k_near_sum<true, false, SPLIT>)
+                : (hw ? k_near_sum<false, true, SPLIT> : k_near_sum<false, false, SPLIT>);
+    k<<<c->ns, kNearThreads, 0, c->s>>>(c->ns, alpha, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
+                                       c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
+                                       c->d_n, d_far, c->d_b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
+{
+    return c->split ? near_dispatch<true>(c, alpha, d_exc, d_far) : near_dispatch<false>(c, alpha, d_exc, d_far);
+}
+
+__device__ __forceinline__ float2 split2(double v)
+{
+    float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// In-place conversion of FP64 values to (hi, lo) float pairs.
+__global__ void k_split_inplace(int64_t n, double *v)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double x = v[k];
+        reinterpret_cast<float2 *>(v)[k] = split2(x);
+    }
+}
+
+// Float-pair copies of FP64 values.
+__global__ void k_split_copy(int64_t n, const double *__restrict__ v, float2 *out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = split2(v[k]);
+}
+
+cudaError_t launch_split_coefficients(tdbem_ctx *c)
+{
+    if (c->d_ku) k_split_inplace<<<152 * 16, 256, 0, c->s>>>(c->ncoef, c->d_ku);
+    if (c->d_kw) k_split_inplace<<<152 * 16, 256, 0, c->s>>>(c->ncoef, c->d_kw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_histories(tdbem_ctx *c)
+{
+    int64_t n = (int64_t)c->P.nt * c->ns;
+    k_split_copy<<<152 * 16, 256, 0, c->s>>>(n, c->d_u, c->d_us);
+    k_split_copy<<<152 * 16, 256, 0, c->s>>>(n, c->d_q, c->d_qs);
     return cudaGetLastError();
 }
 
@@ -91,27 +254,27 @@ cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc)
 // R in the ELL store).  it = 0 starts from x = D^-1 b.  The last sweep adds
 // the solution to the unknown component of step a-1 (u where phi = 1, q
 // where phi = 0) and flags a non-finite value (flag bit 1).
-__global__ void k_jacobi(int ns, const double *__restrict__ aoff, const int32_t *__restrict__ acol,
+__global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, const int32_t *__restrict__ acol,
                          const double *__restrict__ ainv, const double *__restrict__ b,
                          const double *__restrict__ xin, double *xout, int last, int64_t row,
-                         const int8_t *__restrict__ phi, double *u, double *q, int *flag)
+                         const int8_t *__restrict__ phi, double *u, double *q, float2 *us, float2 *qs,
+                         int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     double s = b[i];
     if (xin) {
-#pragma unroll
-        for (int k = 0; k < kEllWidth; ++k) {
+        for (int k = 0; k < width; ++k) {
             int cidx = acol[(int64_t)k * ns + i];
             if (cidx >= 0) s -= aoff[(int64_t)k * ns + i] * xin[cidx];
         }
     }
     double x = s * ainv[i];
     if (last) {
-        if (phi[i])
-            u[row + i] += x;
-        else
-            q[row + i] += x;
+        double *h = phi[i] ? u : q;
+        double v = h[row + i] + x;
+        h[row + i] = v;
+        if (us) (phi[i] ? us : qs)[row + i] = split2(v);
         if (!isfinite(x)) atomicOr(flag, 1);
     } else {
         xout[i] = x;
@@ -123,8 +286,9 @@ cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last)
     const double *xin = (it == 0) ? nullptr : ((it & 1) ? c->d_xa : c->d_xb);
     double *xout = (it & 1) ? c->d_xb : c->d_xa;
     int64_t row = (int64_t)(alpha - 1) * c->ns;
-    k_jacobi<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, xout, last,
-                                                   row, c->d_phi, c->d_u, c->d_q, c->d_flag);
+    k_jacobi<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->ell_w, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, xout, last,
+                                                   row, c->d_phi, c->d_u, c->d_q, c->d_us, c->d_qs,
+                                                   c->d_flag);
     return cudaGetLastError();
 }
 

@@ -16,8 +16,6 @@ namespace tdbem {
 constexpr int kG0Bits = 12;
 constexpr int kMaxG0 = (1 << kG0Bits) - 1;
 constexpr int kMaxCnt = 15;
-// Zero-lag matrix: off-diagonal entries per row (ELL width).
-constexpr int kEllWidth = 8;
 
 // Coefficient kinds (bit positions in a kinds mask).
 enum { KIND_CU = 0, KIND_CW = 1, KIND_UB = 2, KIND_WB = 3 };
@@ -29,12 +27,61 @@ struct Incident {
     double t0, width, c, dt;
 };
 
+// One level of the spatial hierarchy (device arrays).
+struct TreeLevel {
+    int nc = 0;                   // occupied cells
+    uint64_t *ckey = nullptr;     // [nc] Morton keys, increasing
+    int32_t *cstart = nullptr;    // [nc+1] first sorted position of each cell
+    int32_t *ecell = nullptr;     // [ns] cell of each sorted position
+    int32_t *nbr = nullptr;       // [nc][27] neighbour cells, by key
+    int32_t *ncount = nullptr;    // [nc]
+    int32_t *il = nullptr;        // [nc][189] interaction list, by key (levels >= 2)
+    int32_t *ilcount = nullptr;   // [nc]
+};
+
+struct Tree {
+    double *box = nullptr;        // lo[3], side
+    uint64_t *key = nullptr;      // [ns] leaf keys (element numbering)
+    int32_t *perm = nullptr;      // [ns] element at each sorted position
+    int32_t *e2c = nullptr;       // [ns] leaf cell of each element (element numbering)
+    std::vector<TreeLevel> levels;
+};
+
+// One level of the space-time FMM (device arrays; levels 2..L).
+struct FmmLevel {
+    int nc = 0;
+    double s = 0, hs = 0;        // cell side, interpolation half-width
+    int T = 0;                   // steps per interval
+    double Tlen = 0;             // c x interval length (T of Formula 1)
+    double *M = nullptr;         // [nc][P] moment of the current source interval
+    double *ring = nullptr;      // [mu+2][nc][P] locals L_k .. L_{k+mu+1}
+    double *D = nullptr;         // [d][nc][P] derivative locals L^(p)
+    double *A = nullptr;         // [n_d][nc][P] auxiliary locals L^(p,m)
+    double *G = nullptr;         // [d][nc][P] contributions L^(p)_{k+mu+1,k}
+    double *op = nullptr;        // [343][mu+1+d][P][P] M2L operators
+    double *Sm = nullptr;        // [2][ps][ps] transfer to the parent level
+};
+
+struct Fmm {
+    bool on = false;
+    int L = 0, ps = 0, pt = 0, P3 = 0, P = 0, mu = 0, Lt = 0, nblk = 0, nd = 0, nslot = 0;
+    double rho = 0;
+    std::vector<FmmLevel> lev;
+    double *At = nullptr, *As = nullptr, *Dv = nullptr, *Dn = nullptr;  // [ns][P3]
+    double *tl = nullptr, *dtl = nullptr;  // [Lt][8] time basis at the interval's positions
+    double *wk = nullptr;                   // [d+2] w^{kappa,d}
+    double *Tm = nullptr;                   // [2][pt][pt] time transfer
+    double *cmp = nullptr;                  // c_m^p(k) of the current call
+    double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
+    int far_k = -1;                         // leaf interval the far field belongs to
+};
+
 struct Pending {
     int phase;
     cudaEvent_t a, b;
 };
 
-enum { PH_RHS = 0, PH_NEAR = 1, PH_SOLVE = 2, PH_COUNT = 3 };
+enum { PH_RHS = 0, PH_NEAR = 1, PH_SOLVE = 2, PH_FAR = 3, PH_COUNT = 4 };
 
 struct Status {
     int code = TDBEM_OK;
@@ -71,19 +118,28 @@ struct tdbem_ctx {
     double *d_xc = nullptr;  // [ns][3] centroids (physical)
     double *d_n = nullptr;   // [ns][3] the paper's normal (into V)
     int8_t *d_phi = nullptr;
-    uint16_t *d_meta = nullptr;  // [ns][ns] lag windows
-    int32_t *d_btot = nullptr;   // [ns][nblk] coefficients per 32-pair block
-    int64_t *d_boff = nullptr;   // [ns][nblk] first coefficient of each block
-    int nblk = 0;
+    // pair lists: row i owns pairs [prow[i], prow[i+1]) with columns col[p]
+    // (nullptr: all columns, j = p - prow[i]), cut into 32-pair blocks
+    // [rowblk[i], rowblk[i+1])
+    int64_t *d_prow = nullptr;   // [ns+1]
+    int32_t *d_col = nullptr;    // [npairs] or nullptr
+    int64_t *d_rowblk = nullptr; // [ns+1]
+    int64_t nbt = 0;             // blocks in total
+    uint16_t *d_meta = nullptr;  // [npairs] lag windows
+    int32_t *d_btot = nullptr;   // [nbt] coefficients per 32-pair block
+    int64_t *d_boff = nullptr;   // [nbt] first coefficient of each block
     int smax = 0;                // largest window length
     int gmax = 0;                // largest lag stored
     int64_t npairs = 0, ncoef = 0;
     int ku_kind = -1, kw_kind = -1;
     double *d_ku = nullptr, *d_kw = nullptr;
     double *d_u = nullptr, *d_q = nullptr;  // [nt][ns] histories
+    bool split = false;                     // split-precision history sum
+    float2 *d_us = nullptr, *d_qs = nullptr; // [nt][ns] float-pair copies (split only)
     double *d_b = nullptr, *d_xa = nullptr, *d_xb = nullptr;
-    double *d_aoff = nullptr;    // [kEllWidth][ns]
-    int32_t *d_acol = nullptr;   // [kEllWidth][ns]
+    int ell_w = 0;               // off-diagonal entries per row of the zero-lag store
+    double *d_aoff = nullptr;    // [ell_w][ns]
+    int32_t *d_acol = nullptr;   // [ell_w][ns]
     double *d_ainv = nullptr;    // [ns]
     int solve_iters = 0;
     double contraction = 0.0;
@@ -94,11 +150,14 @@ struct tdbem_ctx {
     int *d_flag = nullptr;       // device error flags
     std::vector<void *> allocs;  // every cudaMalloc of the context
 
+    tdbem::Tree tree;  // built when P.depth > 0
+    tdbem::Fmm fmm;    // algo 1
+
     // timing
     std::vector<tdbem::Pending> pending;
     std::vector<cudaEvent_t> pool;
-    double ms[tdbem::PH_COUNT] = {0, 0, 0};
-    int64_t launches[tdbem::PH_COUNT] = {0, 0, 0};
+    double ms[tdbem::PH_COUNT] = {0, 0, 0, 0};
+    int64_t launches[tdbem::PH_COUNT] = {0, 0, 0, 0};
     int64_t steps_total = 0;
     double ms_prepare = 0.0;
 };
@@ -108,15 +167,25 @@ namespace tdbem {
 // Kernel launchers (coef.cu)
 cudaError_t launch_geometry(tdbem_ctx *c);
 cudaError_t launch_windows(tdbem_ctx *c, int *d_maxcnt, int *d_maxg0, int *d_gtop);
-cudaError_t launch_block_totals(tdbem_ctx *c);
 cudaError_t launch_coefficients(tdbem_ctx *c);
-cudaError_t launch_zero_lag(tdbem_ctx *c);
+cudaError_t launch_zero_lag(tdbem_ctx *c, bool count_only);
 void set_bspline_table(const BsTable &T, cudaStream_t s);
 cudaError_t launch_known_collocation(tdbem_ctx *c, const double *d_f);
 
+// Hierarchy (tree.cu)
+cudaError_t build_tree(tdbem_ctx *c, std::string &why);
+cudaError_t build_near_lists(tdbem_ctx *c);
+
+// Space-time FMM (fmm.cu)
+cudaError_t fmm_setup(tdbem_ctx *c, std::string &why);
+cudaError_t fmm_boundary(tdbem_ctx *c, int k);
+void free_tree(tdbem_ctx *c);
+
 // Kernel launchers (march.cu)
-cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc);
+cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far);
 cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last);
 cudaError_t launch_gather_x(tdbem_ctx *c, int a0, int nsteps, double *x);
+cudaError_t launch_split_coefficients(tdbem_ctx *c);
+cudaError_t launch_split_histories(tdbem_ctx *c);
 
 }  // namespace tdbem

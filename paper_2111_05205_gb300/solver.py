@@ -17,16 +17,23 @@ class Solver:
     Dirichlet), ``known`` samples of the known data at t_1..t_{nt-1}
     [(nt-1), ns] or None,
     ``incident`` (direction, t0, width) of a Gaussian plane pulse or None.
-    ``stream``: a cudaStream_t handle (int) or None.
+    ``fmm``: (ps, pt, mu) to evaluate the far part with the space-time FMM
+    (needs ``depth`` >= 2; mu = 0 picks the smallest valid value).
+    ``stream``: a cudaStream_t handle (int) or None.  ``precision``: 0 /
+    "fp64" or 1 / "split" (float-pair double-float history sum).
     """
 
     def __init__(self, xyz, tri, c, dt, nt, d, bie, phi=None, known=None, incident=None, stream=None,
-                 solver_tol=0.0, solver_maxit=0):
+                 solver_tol=0.0, solver_maxit=0, precision=0, depth=0, fmm=None):
         p = abi.tdbem_params()
         p.c, p.dt, p.nt, p.d = float(c), float(dt), int(nt), int(d)
         p.bie = {"obie": 0, "bmbie": 1}[bie] if isinstance(bie, str) else int(bie)
         p.algo = 0
-        p.precision = 0
+        p.precision = {"fp64": 0, "split": 1}.get(precision, precision)
+        p.depth = int(depth)
+        if fmm is not None:  # (ps, pt, mu): the space-time FMM for the far part
+            p.algo = 1
+            p.ps, p.pt, p.mu = (int(v) for v in fmm)
         p.solver_tol = float(solver_tol)
         p.solver_maxit = int(solver_maxit)
         self.ns = int(np.asarray(tri).shape[0])

@@ -21,16 +21,16 @@ def phi_of(w):
     return np.full(w.ns, 1 if w.bc == "neumann" else 0, dtype=np.int8)
 
 
-def gpu_solver(w, stream=None):
+def gpu_solver(w, stream=None, precision=0, depth=0, fmm=None):
     from paper_2111_05205_gb300 import Solver
     inc = (w.direction, w.t0, w.sigma) if w.excitation == "plane" else None
     known = known_samples(w) if w.excitation == "uniform" else None
     return Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi_of(w), known=known, incident=inc,
-                  stream=stream)
+                  stream=stream, precision=precision, depth=depth, fmm=fmm)
 
 
-def gpu_march(w):
-    s = gpu_solver(w)
+def gpu_march(w, precision=0):
+    s = gpu_solver(w, precision=precision)
     try:
         s.step()
         u, q = s.solution()

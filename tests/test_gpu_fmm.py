@@ -1,0 +1,78 @@
+"""Parity of the CUDA space-time FMM with the oracle's interpolated far field.
+
+The GPU evaluates the far part of the history sum with P2M at the leaf
+level, separable M2M, the near-/distant-future M2L with the O(Nt)
+recurrence of Formula 1 / Algorithm 1, L2L and L2P (Sections 3-4).  The
+oracle (``oracle.fmm.far_field``) takes the plain route: moments computed
+directly from the elements at every level, the naive M2L of Eq. m2l_actual
+over every past interval with the kernel sampled at the nodes, and L2P.
+M2M and L2L are exact for the interpolating polynomials and Formula 1 is
+exact in the distant-future regime (mu is chosen for that), so the two
+agree to rounding: 1e-10 relative to the largest far value (the recurrence
+carries cancellation between its polynomial terms).  Both sides use the
+GPU's own history as input.  The near lists are bit-exact.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fmm as ofmm
+from oracle import tree as ot
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+CASES = [
+    # name, depth, p, nsteps
+    ("ellipsoid320_bmbie_d2_hard_plane_s7", 2, 3, 37),
+    ("sphere1280_obie_d1_dirichlet_uniform", 3, 2, 29),
+    ("sphere1280_bmbie_d1_dirichlet_uniform", 3, 3, 22),
+]
+
+
+@pytest.mark.parametrize("name,L,p,nsteps", CASES)
+def test_fmm_far_field_matches_oracle(name, L, p, nsteps):
+    _need_gpu()
+    from paper_2111_05205_gb300 import abi
+    from tests.gpu_cases import gpu_solver
+    w = workload(name, nt=nsteps + 2)
+    s = gpu_solver(w, depth=L, fmm=(p, p, 0))
+    try:
+        st = s.stats()
+        H = ofmm.Hierarchy(w.xyz, w.tri, L, w.c, w.dt, w.nt, p, p, w.d)
+        assert (st["fmm_lt"], st["fmm_mu"]) == (H.Lt, H.mu)
+        # near lists bit-exact with the oracle's leaf neighbour lists
+        off = abi.tdbem_get_tree(s.ctx, "near_off")
+        near = abi.tdbem_get_tree(s.ctx, "near")
+        for i in range(w.ns):
+            assert list(near[off[i]:off[i + 1]]) == [int(v) for v in H.T["near"][i]]
+        s.step(nsteps)
+        far, a0 = abi.tdbem_get_far(s.ctx, w.ns)
+        assert a0 > 1
+        u, q = s.solution(0, nsteps)
+        rows = list(range(0, w.ns, max(1, w.ns // 12)))
+        alphas = [a0 + t for t in range(H.Lt)]
+        ref = ofmm.far_field(H, u, q, alphas, w.bie, rows=rows)
+        got = far[:, rows]
+        scale = np.abs(ref).max()
+        assert scale > 0
+        assert np.abs(got - ref).max() <= 1e-10 * scale, (np.abs(got - ref).max(), scale)
+    finally:
+        s.close()
+
+
+def test_fmm_infeasible_hierarchy_is_reported():
+    _need_gpu()
+    from paper_2111_05205_gb300 import abi
+    from tests.gpu_cases import gpu_solver
+    w = workload("ellipsoid320_bmbie_d2_hard_plane_s7", nt=10)
+    with pytest.raises(abi.TdbemError) as e:
+        gpu_solver(w, depth=3, fmm=(3, 3, 0))  # leaf cells smaller than 2 rho
+    assert e.value.code == -7

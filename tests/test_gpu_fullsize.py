@@ -1,0 +1,68 @@
+"""Full-size check (Ns = 20480, the benchmark's workload) of the CUDA direct
+path on sampled outputs the oracle computes one by one:
+
+- the stored Burton-Miller coefficients Wbar of sampled rows against
+  ``oracle.coeffs.rows`` (1e-13 of the largest coefficient);
+- the right-hand side b^{a-1} of sampled rows after a number of steps,
+  against the oracle's history sum of those rows over the GPU's own history
+  (Eq. linear, 1e-12 relative to the sum of magnitudes of the terms);
+- the solution stays finite and the zero-lag solve is a contraction.
+Run in the launch configuration of bench.py (split precision) and in FP64.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import coeffs as oc
+from oracle import mot
+from synth import workload
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def big():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_05205_gb300 import build
+    build.build()
+    w = workload("ellipsoid20480_bmbie_d2_hard_plane", nt=260)
+    rows = np.array([0, 7777, 20479], dtype=np.int32)
+    cdt = w.c * w.dt
+    gm = oc.gamma_max(w.xyz, w.tri, w.d, cdt)
+    C = oc.rows(w.xyz, w.tri, w.d, cdt, rows, kinds=("wb",), gmax=gm)["wb"]
+    return w, rows, C, gm
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_fullsize_sampled_rows(big, precision):
+    from paper_2111_05205_gb300 import abi
+    from tests.gpu_cases import gpu_solver
+    w, rows, C, gm = big
+    s = gpu_solver(w, precision=precision, depth=5 if precision == 1 else 0)
+    try:
+        if precision == 1:
+            from tests.test_gpu_tree import check_tree
+            check_tree(s.ctx, oc.geometry(w.xyz, w.tri)[1], 5)
+        st = s.stats()
+        assert 0 < st["solve_contraction"] < 1
+        G = abi.tdbem_get_coefficients(s.ctx, 3, rows, gm, w.ns)
+        assert np.abs(G - C).max() <= 1e-13 * np.abs(C).max()
+        nstep = 230  # past gamma_max: every lag in use
+        abi.tdbem_step(s.ctx, nstep)
+        b = abi.tdbem_get_rhs(s.ctx, w.ns)
+        u, q = s.solution(0, nstep)
+        assert np.isfinite(u).all()
+        a = nstep
+        v, xc, n, _ = oc.geometry(w.xyz, w.tri)
+        e = mot.incident_rhs(w, xc, n, a)
+        # b = -e + sum_g Wbar^(g) u^{a-g}, with the current unknown u^{a-1} zero
+        uu = u.copy()
+        uu[a - 1] = 0.0
+        for r, i in enumerate(rows):
+            terms = np.concatenate([C[r, g] * uu[a - g] for g in range(1, min(gm, a) + 1)])
+            ref = -e[i] + terms.sum()
+            assert abs(b[i] - ref) <= 1e-12 * (np.abs(terms).sum() + abs(e[i])), (i, b[i], ref)
+    finally:
+        s.close()
