@@ -227,6 +227,24 @@ int tdbem_reset_stats(tdbem_ctx *ctx);
  * error (divergence guard) raised since the last check. */
 int tdbem_sync(tdbem_ctx *ctx);
 
+/* Zero-lag solve that allocates no device memory (the paper has no
+ * counterpart: it is a service for callers that cannot call cudaMalloc at the
+ * point where they solve, e.g. code that runs while someone else captures a
+ * CUDA graph, or hosts that forbid allocation after start-up).  Solves
+ * A x = b with the context's zero-lag matrix (Eq. linear, built by
+ * tdbem_prepare) by the same Jacobi sweeps tdbem_step uses, with its scratch
+ * (b and two iterates) in a fixed file-scope device array of 3 x 262144
+ * doubles (6 MiB) that every GPU loading the library keeps until exit.
+ * b[ns] in, x[ns] out: host buffers (on_device = 0; the call returns after
+ * the copy back) or device buffers (on_device = 1; asynchronous); b and x
+ * must not overlap.  Work goes on the stream given to tdbem_create.
+ * ERR_ARG if ns exceeds 262144.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and should come before any stream capture.  All calls on one device share
+ * the array and it keeps the last call's contents: calls that overlap on the
+ * GPU race.  No cudaMalloc, cudaFree or allocating library call is made. */
+int tdbem_zero_lag_solve_static(const tdbem_ctx *ctx, const double *b, double *x, int32_t on_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,7 @@ SIGNATURES = {
     "tdbem_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(tdbem_stats)]),
     "tdbem_reset_stats": (ctypes.c_int, [_P]),
     "tdbem_sync": (ctypes.c_int, [_P]),
+    "tdbem_zero_lag_solve_static": (ctypes.c_int, [_P, _P, _P, _I]),
 }
 
 _lib = None
@@ -230,3 +231,8 @@ def tdbem_reset_stats(ctx):
 def tdbem_sync(ctx):
     _check(ctx, lib().tdbem_sync(ctx))
 
+
+def tdbem_zero_lag_solve_static(ctx, b, x, on_device=False):
+    """Solve A x = b with no device allocation (see include/tdbem.h).
+    b, x: numpy arrays (host) or torch CUDA tensors (on_device)."""
+    _check(ctx, lib().tdbem_zero_lag_solve_static(ctx, _ptr(b), _ptr(x), int(bool(on_device))))
