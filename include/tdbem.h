@@ -105,6 +105,9 @@ typedef struct {
     double ms_far;                 /* FMM: P2M..L2P at leaf-interval boundaries */
     int64_t launches_far;          /* FMM: boundaries processed */
     int32_t fmm_lt, fmm_mu;        /* FMM: steps per leaf interval, near-future intervals */
+    double ms_m2l;                 /* FMM: gather + M2L GEMMs + reduction, all levels */
+    int64_t launches_m2l;          /* FMM: level M2L applications */
+    double m2l_flops;              /* FMM: 2 (mu+1+d) P^2 per interaction pair and application */
 } tdbem_stats;
 
 /* Creates a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -161,6 +164,56 @@ int tdbem_step(tdbem_ctx *ctx, int32_t nsteps);
  * be NULL (the configured incident wave, if any, is used); x_out may be
  * NULL. */
 int tdbem_step_io(tdbem_ctx *ctx, int32_t nsteps, const double *exc, double *x_out, int32_t on_device);
+
+/* Same as tdbem_step (direct path, algo 0) but every step is one replay of a
+ * CUDA graph that holds the step's kernels (history sum, Jacobi sweeps and a
+ * device-side step counter), captured at the first call: no per-kernel
+ * launch cost.  Results are identical to tdbem_step.  ERR_ARG for algo 1. */
+int tdbem_step_graph(tdbem_ctx *ctx, int32_t nsteps);
+
+/* Batched driver: several independent instances (contexts of the direct
+ * path on one device, e.g. scatterers of different size, order and BIE)
+ * advanced together, each step of all of them one replay of a single CUDA
+ * graph in which every instance's step is an independent branch, so that
+ * small instances share the GPU.  tdbem_batch_create captures the graph
+ * (the contexts must outlive the batch and not be stepped otherwise while
+ * it exists); tdbem_batch_step advances every instance nsteps steps
+ * (asynchronous; ordered after and before each context's stream);
+ * tdbem_batch_sync waits and reports the first device-side error.  Results
+ * are identical to stepping each context alone. */
+typedef struct tdbem_batch tdbem_batch;
+int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out);
+int tdbem_batch_step(tdbem_batch *batch, int32_t nsteps);
+int tdbem_batch_sync(tdbem_batch *batch);
+void tdbem_batch_destroy(tdbem_batch *batch);
+const char *tdbem_batch_last_error(const tdbem_batch *batch);
+
+/* Learned sparse approximate inverse for the zero-lag solve (an addition
+ * of this library; the paper only states that the system is sparse).  A
+ * trainer holds a 2-layer network (3*width inputs -> hidden ReLU -> width
+ * outputs, FP16 weights, FP32 arithmetic) that maps the features of row i
+ * of A (per slot k, the diagonal first and then the off-diagonal entries by
+ * decreasing |A_ij|: A_ij/A_ii, |x_i - x_j|/(c dt), 1) to the row of a
+ * left SAI M on A's pattern (M_ij = output_k / A_ii).  Training minimises
+ * sum_i ||e_i^T - m_i^T A||^2 over the rows of prepared contexts (their
+ * zero-lag matrices; a context with nt = 2 computes only those) with Adam,
+ * one update per context and pass, all on the GPU.  width 2..16, hidden
+ * 1..64; the weights start from Jacobi (M = D^-1). */
+typedef struct tdbem_sai tdbem_sai;
+int tdbem_sai_create(int32_t width, int32_t hidden, uint64_t seed, tdbem_sai **out);
+void tdbem_sai_destroy(tdbem_sai *sai);
+const char *tdbem_sai_last_error(const tdbem_sai *sai);
+int tdbem_sai_train(tdbem_sai *sai, tdbem_ctx *const *ctxs, int32_t n, int32_t epochs, float lr, float *loss_out);
+/* Loss (sum over rows) and gradient (grad[count], FP32) at the current weights. */
+int tdbem_sai_gradient(tdbem_sai *sai, tdbem_ctx *ctx, float *grad, float *loss);
+/* Weights: *count = their number; set = 0 copies the FP16 weights (as
+ * floats) to inout, set = 1 loads inout (and resets the optimiser). */
+int tdbem_sai_weights(tdbem_sai *sai, float *inout, int64_t *count, int32_t set);
+/* Installs the network's M as the context's zero-lag solver (sweeps
+ * x <- x + M (b - A x), count from ||I - M A||_inf so that the error stays
+ * below solver_tol) when that takes fewer launches than Jacobi; otherwise
+ * Jacobi stays.  *use_sai, *sweeps, *contraction report the choice. */
+int tdbem_set_precond(tdbem_ctx *ctx, const tdbem_sai *sai, int32_t *use_sai, int32_t *sweeps, double *contraction);
 
 /* Number of time steps taken so far (a_cur). */
 int tdbem_steps_done(const tdbem_ctx *ctx, int32_t *out);

@@ -40,7 +40,8 @@ class tdbem_stats(ctypes.Structure):
                 ("gamma_max", ctypes.c_int32), ("solve_iters", ctypes.c_int32),
                 ("solve_contraction", ctypes.c_double), ("ms_prepare", ctypes.c_double),
                 ("ms_far", ctypes.c_double), ("launches_far", ctypes.c_int64), ("fmm_lt", ctypes.c_int32),
-                ("fmm_mu", ctypes.c_int32)]
+                ("fmm_mu", ctypes.c_int32), ("ms_m2l", ctypes.c_double), ("launches_m2l", ctypes.c_int64),
+                ("m2l_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,6 +62,19 @@ SIGNATURES = {
     "tdbem_prepare": (ctypes.c_int, [_P]),
     "tdbem_step": (ctypes.c_int, [_P, _I]),
     "tdbem_step_io": (ctypes.c_int, [_P, _I, _P, _P, _I]),
+    "tdbem_step_graph": (ctypes.c_int, [_P, _I]),
+    "tdbem_sai_create": (ctypes.c_int, [_I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "tdbem_sai_destroy": (None, [_P]),
+    "tdbem_sai_last_error": (ctypes.c_char_p, [_P]),
+    "tdbem_sai_train": (ctypes.c_int, [_P, ctypes.POINTER(_P), _I, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "tdbem_sai_gradient": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "tdbem_sai_weights": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _I]),
+    "tdbem_set_precond": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tdbem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "tdbem_batch_step": (ctypes.c_int, [_P, _I]),
+    "tdbem_batch_sync": (ctypes.c_int, [_P]),
+    "tdbem_batch_destroy": (None, [_P]),
+    "tdbem_batch_last_error": (ctypes.c_char_p, [_P]),
     "tdbem_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_I)]),
     "tdbem_get_solution": (ctypes.c_int, [_P, _P, _P, _I, _I, _I]),
     "tdbem_get_rhs": (ctypes.c_int, [_P, _P]),
@@ -159,6 +173,101 @@ def tdbem_step(ctx, nsteps):
 def tdbem_step_io(ctx, nsteps, exc=None, x_out=None, on_device=False):
     """exc / x_out: numpy arrays (host) or torch CUDA tensors (on_device)."""
     _check(ctx, lib().tdbem_step_io(ctx, int(nsteps), _ptr(exc), _ptr(x_out), int(bool(on_device))))
+
+
+def tdbem_step_graph(ctx, nsteps):
+    _check(ctx, lib().tdbem_step_graph(ctx, int(nsteps)))
+
+
+def _bcheck(batch, code):
+    if code != TDBEM_OK:
+        m = lib().tdbem_batch_last_error(batch)
+        raise TdbemError(code, m.decode() if m else "")
+
+
+def tdbem_batch_create(ctxs):
+    arr = (_P * len(ctxs))(*ctxs)
+    out = _P()
+    code = lib().tdbem_batch_create(arr, len(ctxs), ctypes.byref(out))
+    if code != TDBEM_OK:
+        raise TdbemError(code, "tdbem_batch_create")
+    return out.value
+
+
+def tdbem_batch_step(batch, nsteps):
+    _bcheck(batch, lib().tdbem_batch_step(batch, int(nsteps)))
+
+
+def tdbem_batch_sync(batch):
+    _bcheck(batch, lib().tdbem_batch_sync(batch))
+
+
+def tdbem_batch_destroy(batch):
+    lib().tdbem_batch_destroy(batch)
+
+
+def tdbem_batch_last_error(batch):
+    m = lib().tdbem_batch_last_error(batch)
+    return m.decode() if m else ""
+
+
+def _scheck(sai, code):
+    if code != TDBEM_OK:
+        m = lib().tdbem_sai_last_error(sai)
+        raise TdbemError(code, m.decode() if m else "")
+
+
+def tdbem_sai_create(width, hidden, seed):
+    out = _P()
+    code = lib().tdbem_sai_create(int(width), int(hidden), int(seed), ctypes.byref(out))
+    if code != TDBEM_OK:
+        raise TdbemError(code, "tdbem_sai_create")
+    return out.value
+
+
+def tdbem_sai_destroy(sai):
+    lib().tdbem_sai_destroy(sai)
+
+
+def tdbem_sai_last_error(sai):
+    m = lib().tdbem_sai_last_error(sai)
+    return m.decode() if m else ""
+
+
+def tdbem_sai_train(sai, ctxs, epochs, lr):
+    arr = (_P * len(ctxs))(*ctxs)
+    loss = ctypes.c_float()
+    _scheck(sai, lib().tdbem_sai_train(sai, arr, len(ctxs), int(epochs), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def tdbem_sai_weights(sai, values=None):
+    """Get (values None) or set the network weights (float32 numpy)."""
+    n = ctypes.c_int64()
+    _scheck(sai, lib().tdbem_sai_weights(sai, None, ctypes.byref(n), 0))
+    if values is None:
+        out = np.zeros(n.value, dtype=np.float32)
+        _scheck(sai, lib().tdbem_sai_weights(sai, _ptr(out), ctypes.byref(n), 0))
+        return out
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    assert v.size == n.value
+    _scheck(sai, lib().tdbem_sai_weights(sai, _ptr(v), ctypes.byref(n), 1))
+    return v
+
+
+def tdbem_sai_gradient(sai, ctx):
+    n = ctypes.c_int64()
+    _scheck(sai, lib().tdbem_sai_weights(sai, None, ctypes.byref(n), 0))
+    g = np.zeros(n.value, dtype=np.float32)
+    loss = ctypes.c_float()
+    _scheck(sai, lib().tdbem_sai_gradient(sai, ctx, _ptr(g), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def tdbem_set_precond(ctx, sai):
+    use, sw, q = _I(), _I(), _D()
+    _check(ctx, lib().tdbem_set_precond(ctx, sai, ctypes.byref(use), ctypes.byref(sw), ctypes.byref(q)))
+    return bool(use.value), sw.value, q.value
 
 
 def tdbem_steps_done(ctx):

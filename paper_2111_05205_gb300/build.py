@@ -45,9 +45,10 @@ def build(force=False, verbose=False):
     if not force and not _stale(LIB, deps):
         return LIB
     nvcc = _nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                    "-Xptxas", "-v"] if verbose else ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
-                                                              "-fPIC", "--expt-relaxed-constexpr"]
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+                    "-ffp-contract=off", "--expt-relaxed-constexpr", "-Xptxas", "-v"] if verbose else ARCH + [
+        "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+        "--expt-relaxed-constexpr"]
     objs = []
 
     def one(src):
@@ -64,7 +65,7 @@ def build(force=False, verbose=False):
                 print(log)
     tmp = LIB + ".%d.tmp" % os.getpid()
     r = subprocess.run([nvcc, "-shared", "-o", tmp] + objs + ARCH + [
-        "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64"], capture_output=True, text=True)
+        "-cudart", "shared", "-lcublas", "-Xlinker", "-rpath,/usr/local/cuda/lib64"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)

@@ -2,6 +2,7 @@
 // time-marching driver (Section 2.5, Eq. linear).
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -104,6 +105,24 @@ struct PhaseTimer {
     }
 };
 
+}  // namespace
+
+void tdbem::phase_begin(tdbem_ctx *c, cudaEvent_t *e)
+{
+    if (c->pending.size() > 8192) harvest(c);
+    *e = take_event(c);
+    cudaEventRecord(*e, c->s);
+}
+
+void tdbem::phase_end(tdbem_ctx *c, int phase, cudaEvent_t a)
+{
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->s);
+    c->pending.push_back({phase, a, b});
+}
+
+namespace {
+
 int check_flags(tdbem_ctx *c)
 {
     int f = 0;
@@ -154,8 +173,10 @@ void tdbem_destroy(tdbem_ctx *c)
     if (c->s) cudaStreamSynchronize(c->s);
     harvest(c);
     for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     for (void *p : c->allocs) cudaFree(p);
     free_tree(c);
+    fmm_free(c);
     if (c->s) cudaStreamDestroy(c->s);
     delete c;
 }
@@ -306,7 +327,7 @@ int tdbem_prepare(tdbem_ctx *c)
     // lag windows of the pairs and coefficients per 32-pair block
     TD_CUDA(dalloc(c, &c->d_meta, (size_t)c->npairs));
     TD_CUDA(dalloc(c, &c->d_btot, (size_t)c->nbt));
-    TD_CUDA(dalloc(c, &c->d_boff, (size_t)c->nbt));
+    TD_CUDA(dalloc(c, &c->d_boff, (size_t)c->nbt + 1));
     int *d_m = c->d_flag + 1;  // flag[1..3]: max cnt, max g0, max lag
     TD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->s));
     TD_CUDA(launch_windows(c, d_m, d_m + 1, d_m + 2));
@@ -331,13 +352,15 @@ int tdbem_prepare(tdbem_ctx *c)
             run += tot[k];
         }
         c->ncoef = run;
-        TD_CUDA(cudaMemcpyAsync(c->d_boff, off.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+        off.push_back(run);
+        TD_CUDA(cudaMemcpyAsync(c->d_boff, off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
         TD_CUDA(cudaStreamSynchronize(c->s));
     }
 
     // influence coefficients
-    if (c->ku_kind >= 0) TD_CUDA(dalloc(c, &c->d_ku, (size_t)c->ncoef));
-    if (c->kw_kind >= 0) TD_CUDA(dalloc(c, &c->d_kw, (size_t)c->ncoef));
+    if (c->ku_kind >= 0) TD_CUDA(dalloc(c, &c->d_ku, (size_t)c->ncoef + 2));
+    if (c->kw_kind >= 0) TD_CUDA(dalloc(c, &c->d_kw, (size_t)c->ncoef + 2));
+
     TD_CUDA(launch_coefficients(c));
 
     // zero-lag matrix (width of its ELL store counted first) and the Jacobi
@@ -407,6 +430,7 @@ int tdbem_prepare(tdbem_ctx *c)
     TD_CUDA(dalloc(c, &c->d_b, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xa, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xb, (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_r, (size_t)ns));
     TD_CUDA(cudaMemsetAsync(c->d_b, 0, ns * sizeof(double), c->s));
     TD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->s));
     TD_CUDA(cudaStreamSynchronize(c->s));
@@ -444,13 +468,71 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
         c->launches[PH_NEAR] += 1;
         {
             PhaseTimer t(c, PH_SOLVE);
-            for (int it = 0; it < c->solve_iters; ++it)
-                TD_CUDA(launch_jacobi(c, alpha, it, it == c->solve_iters - 1));
+            if (c->sai_val) {
+                for (int it = 0; it < c->sai_iters; ++it) TD_CUDA(launch_sai_sweep(c, alpha, it));
+            } else {
+                for (int it = 0; it < c->solve_iters; ++it)
+                    TD_CUDA(launch_jacobi(c, alpha, it, it == c->solve_iters - 1));
+            }
         }
-        c->launches[PH_SOLVE] += c->solve_iters;
+        c->launches[PH_SOLVE] += c->sai_val ? 2 * c->sai_iters : c->solve_iters;
         c->alpha = alpha;
         c->steps_total += 1;
     }
+    return TDBEM_OK;
+}
+
+// Kernels of one direct-path step reading the step index from d_alpha,
+// launched on `st` (a stream being captured).
+static cudaError_t launch_step_chain(tdbem_ctx *c, cudaStream_t st)
+{
+    cudaStream_t keep = c->s;
+    c->s = st;
+    c->alpha_dev_on = true;
+    cudaError_t e = launch_near_sum(c, 0, nullptr, nullptr);
+    for (int it = 0; it < c->solve_iters && e == cudaSuccess; ++it) e = launch_jacobi(c, 0, it, it == c->solve_iters - 1);
+    if (e == cudaSuccess) e = launch_alpha_next(c);
+    c->alpha_dev_on = false;
+    c->s = keep;
+    return e;
+}
+
+static int graph_ready(tdbem_ctx *c)
+{
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "graph step before prepare");
+    if (c->fmm.on) return fail(c, TDBEM_ERR_ARG, "graph-replayed steps are for the direct path (algo 0)");
+    if (c->sai_val) return fail(c, TDBEM_ERR_ARG, "graph-replayed steps use the Jacobi zero-lag solve");
+    if (!c->d_alpha) TD_CUDA(dalloc(c, &c->d_alpha, 1));
+    return TDBEM_OK;
+}
+
+int tdbem_step_graph(tdbem_ctx *c, int32_t nsteps)
+{
+    if (!c) return TDBEM_ERR_ARG;
+    int r = graph_ready(c);
+    if (r != TDBEM_OK) return r;
+    if (nsteps < 0 || c->alpha + nsteps > c->P.nt - 1) return fail(c, TDBEM_ERR_ARG, "stepping past Nt-1");
+    if (nsteps == 0) return TDBEM_OK;
+    TD_CUDA(cudaSetDevice(c->dev));
+    if (!c->graph) {
+        cudaGraph_t g;
+        TD_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_step_chain(c, c->s);
+        cudaError_t e2 = cudaStreamEndCapture(c->s, &g);
+        TD_CUDA(e);
+        TD_CUDA(e2);
+        TD_CUDA(cudaGraphInstantiate(&c->graph, g, 0));
+        cudaGraphDestroy(g);
+    }
+    TD_CUDA(join(c->user, c->s));
+    int a = c->alpha + 1;
+    TD_CUDA(cudaMemcpyAsync(c->d_alpha, &a, sizeof(int), cudaMemcpyHostToDevice, c->s));
+    for (int n = 0; n < nsteps; ++n) TD_CUDA(cudaGraphLaunch(c->graph, c->s));
+    c->launches[PH_NEAR] += nsteps;
+    c->launches[PH_SOLVE] += (int64_t)nsteps * c->solve_iters;
+    c->alpha += nsteps;
+    c->steps_total += nsteps;
+    TD_CUDA(join(c->s, c->user));
     return TDBEM_OK;
 }
 
@@ -725,6 +807,9 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->ms_near = c->ms[PH_NEAR];
     o->ms_solve = c->ms[PH_SOLVE];
     o->ms_far = c->ms[PH_FAR];
+    o->ms_m2l = c->ms[PH_M2L];
+    o->launches_m2l = c->launches[PH_M2L];
+    o->m2l_flops = c->m2l_flops;
     o->launches_far = c->launches[PH_FAR];
     o->fmm_lt = c->fmm.Lt;
     o->fmm_mu = c->fmm.mu;
@@ -756,6 +841,7 @@ int tdbem_reset_stats(tdbem_ctx *c)
         c->launches[k] = 0;
     }
     c->steps_total = 0;
+    c->m2l_flops = 0.0;
     return TDBEM_OK;
 }
 
@@ -766,5 +852,125 @@ int tdbem_sync(tdbem_ctx *c)
     TD_CUDA(cudaGetLastError());
     return check_flags(c);
 }
+
+struct tdbem_batch {
+    std::vector<tdbem_ctx *> ctx;
+    cudaStream_t s = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::string err;
+};
+
+int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out)
+{
+    if (!ctxs || n < 1 || !out) return TDBEM_ERR_ARG;
+    *out = nullptr;
+    int dev = ctxs[0] ? ctxs[0]->dev : -1;
+    for (int k = 0; k < n; ++k) {
+        tdbem_ctx *c = ctxs[k];
+        if (!c || c->dev != dev) return TDBEM_ERR_ARG;
+        for (int m = 0; m < k; ++m)
+            if (ctxs[m] == c) return TDBEM_ERR_ARG;
+        int r = graph_ready(c);
+        if (r != TDBEM_OK) return r;
+    }
+    tdbem_batch *B = new tdbem_batch();
+    B->ctx.assign(ctxs, ctxs + n);
+    cudaError_t e = cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking);
+    B->ev.resize(n + 1);
+    for (auto &x : B->ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    // one graph: every instance's step chain is an independent branch
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(B->ev[n], B->s);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        tdbem_ctx *c = B->ctx[k];
+        e = cudaStreamWaitEvent(c->s, B->ev[n], 0);
+        if (e == cudaSuccess) e = launch_step_chain(c, c->s);
+        if (e == cudaSuccess) e = cudaEventRecord(B->ev[k], c->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->s, B->ev[k], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(B->s, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        tdbem_batch_destroy(B);
+        return TDBEM_ERR_CUDA;
+    }
+    *out = B;
+    return TDBEM_OK;
+}
+
+int tdbem_batch_step(tdbem_batch *B, int32_t nsteps)
+{
+    if (!B || nsteps < 0) return TDBEM_ERR_ARG;
+    for (tdbem_ctx *c : B->ctx)
+        if (c->alpha + nsteps > c->P.nt - 1) {
+            B->err = "an instance would step past its Nt-1";
+            return TDBEM_ERR_ARG;
+        }
+    if (nsteps == 0) return TDBEM_OK;
+    for (tdbem_ctx *c : B->ctx) {
+        cudaError_t e = join(c->user, B->s);
+        int a = c->alpha + 1;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_alpha, &a, sizeof(int), cudaMemcpyHostToDevice, B->s);
+        if (e != cudaSuccess) {
+            B->err = cudaGetErrorString(e);
+            return TDBEM_ERR_CUDA;
+        }
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        cudaError_t e = cudaGraphLaunch(B->graph, B->s);
+        if (e != cudaSuccess) {
+            B->err = cudaGetErrorString(e);
+            return TDBEM_ERR_CUDA;
+        }
+    }
+    for (tdbem_ctx *c : B->ctx) {
+        c->alpha += nsteps;
+        c->steps_total += nsteps;
+        c->launches[PH_NEAR] += nsteps;
+        c->launches[PH_SOLVE] += (int64_t)nsteps * c->solve_iters;
+        cudaError_t e = join(B->s, c->user);
+        if (e != cudaSuccess) {
+            B->err = cudaGetErrorString(e);
+            return TDBEM_ERR_CUDA;
+        }
+    }
+    return TDBEM_OK;
+}
+
+int tdbem_batch_sync(tdbem_batch *B)
+{
+    if (!B) return TDBEM_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(B->s);
+    if (e != cudaSuccess) {
+        B->err = cudaGetErrorString(e);
+        return TDBEM_ERR_CUDA;
+    }
+    for (tdbem_ctx *c : B->ctx) {
+        int r = check_flags(c);
+        if (r != TDBEM_OK) {
+            B->err = c->err;
+            return r;
+        }
+    }
+    return TDBEM_OK;
+}
+
+void tdbem_batch_destroy(tdbem_batch *B)
+{
+    if (!B) return;
+    if (B->s) cudaStreamSynchronize(B->s);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    for (auto e : B->ev)
+        if (e) cudaEventDestroy(e);
+    if (B->s) cudaStreamDestroy(B->s);
+    delete B;
+}
+
+const char *tdbem_batch_last_error(const tdbem_batch *B) { return B ? B->err.c_str() : "null batch"; }
 
 }  // extern "C"

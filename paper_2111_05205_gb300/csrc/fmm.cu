@@ -21,6 +21,8 @@
 
 #include <algorithm>
 
+#include <cublas_v2.h>
+
 #include "tdbem_internal.cuh"
 
 namespace tdbem {
@@ -402,6 +404,45 @@ __global__ void k_l2p(int ns, int P3, int pt, int Lt, int bie, double c, const i
 
 namespace tdbem {
 
+// M2L as dense GEMMs grouped by cell offset: the moments of the source
+// cells of every interaction pair, ordered by (offset, observation cell),
+// are gathered into the columns of B; for each offset one GEMM multiplies
+// the offset's operator stack [(mu+1+d) P x P] with its slice of B; the
+// per-cell sums over the cell's pairs (fixed order) feed the locals.
+template <typename TB>
+__global__ void k_m2l_gather(int64_t np, int P, const int32_t *__restrict__ pS, const int64_t *__restrict__ pcol,
+                             const double *__restrict__ M, TB *B)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * P; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pr = e / P;
+        int r = (int)(e % P);
+        B[pcol[pr] * P + r] = (TB)M[(int64_t)pS[pr] * P + r];
+    }
+}
+
+__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *b)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+template <typename TC>
+__global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
+                             const int64_t *__restrict__ oidx, const TC *__restrict__ C, double *ring, double *G)
+{
+    const int R = nblk * P;
+    int O = blockIdx.x;
+    for (int e = threadIdx.x; e < R; e += blockDim.x) {
+        double s = 0.0;
+        for (int64_t t = ooff[O]; t < ooff[O + 1]; ++t) s += (double)C[(int64_t)oidx[t] * R + e];
+        int blk = e / P, r = e % P;
+        if (blk <= mu)
+            ring[((int64_t)((k + blk + 1) % nslot) * nc + O) * P + r] += s;
+        else
+            G[((int64_t)(blk - mu - 1) * nc + O) * P + r] = s;
+    }
+}
+
 namespace {
 
 double h_cheb(int p, int a) { return cos((2.0 * a + 1.0) * M_PI / (2.0 * p)); }
@@ -535,6 +576,10 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     F.nd = d * (d - 1) / 2;
     F.nslot = F.mu + 2;
     const int P = F.P, P3 = F.P3, ps = F.ps, pt = F.pt;
+    if (cublasCreate(&F.blas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    cublasSetStream(F.blas, c->s);
+    cublasSetMathMode(F.blas, CUBLAS_DEFAULT_MATH);
+    if (c->split) cublasSetEmulationStrategy(F.blas, CUBLAS_EMULATION_STRATEGY_EAGER);
 
     // per-element tables (leaf boxes)
     F_TRY(falloc(c, &F.At, (size_t)ns * P3));
@@ -615,10 +660,83 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         }
         size_t nop = (size_t)343 * F.nblk * P * P;
         F_TRY(falloc(c, &V.op, nop));
+        // interaction pairs grouped by offset, and per observation cell
+        {
+            const TreeLevel &T = c->tree.levels[l];
+            std::vector<int32_t> cnt(V.nc), il((size_t)V.nc * 189);
+            std::vector<uint64_t> keys(V.nc);
+            F_TRY(cudaMemcpy(cnt.data(), T.ilcount, V.nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            F_TRY(cudaMemcpy(il.data(), T.il, il.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            F_TRY(cudaMemcpy(keys.data(), T.ckey, V.nc * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+            auto coord = [&](uint64_t key, int a) {
+                int v = 0;
+                for (int b = 0; b < l; ++b) v |= (int)((key >> (3 * b + a)) & 1u) << b;
+                return v;
+            };
+            std::vector<std::vector<std::pair<int, int>>> byoff(343);
+            for (int O = 0; O < V.nc; ++O)
+                for (int t = 0; t < cnt[O]; ++t) {
+                    int S = il[(size_t)O * 189 + t];
+                    int o = (coord(keys[S], 0) - coord(keys[O], 0) + 3) +
+                            7 * ((coord(keys[S], 1) - coord(keys[O], 1) + 3) + 7 * (coord(keys[S], 2) - coord(keys[O], 2) + 3));
+                    byoff[o].push_back({O, S});
+                }
+            std::vector<int32_t> pS, pO;
+            V.ostart.assign(344, 0);
+            for (int o = 0; o < 343; ++o) {
+                V.ostart[o] = (int64_t)pS.size();
+                for (auto &pr : byoff[o]) {
+                    pO.push_back(pr.first);
+                    pS.push_back(pr.second);
+                }
+            }
+            V.ostart[343] = (int64_t)pS.size();
+            V.np = (int64_t)pS.size();
+            // every offset's pairs occupy a slab of nmax columns (zero-padded)
+            // so that one strided-batched GEMM covers all offsets
+            V.nmax = 0;
+            for (int o = 0; o < 343; ++o) V.nmax = std::max<int64_t>(V.nmax, V.ostart[o + 1] - V.ostart[o]);
+            std::vector<int64_t> pcol(V.np);
+            for (int o = 0; o < 343; ++o)
+                for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = (int64_t)o * V.nmax + (t - V.ostart[o]);
+            std::vector<int64_t> ooff(V.nc + 1, 0);
+            for (int32_t O : pO) ooff[O + 1]++;
+            for (int O = 0; O < V.nc; ++O) ooff[O + 1] += ooff[O];
+            std::vector<int64_t> oidx(V.np), fill(ooff.begin(), ooff.end() - 1);
+            for (int64_t t = 0; t < V.np; ++t) oidx[fill[pO[t]]++] = pcol[t];
+            F_TRY(falloc(c, &V.pS, (size_t)V.np));
+            F_TRY(falloc(c, &V.pcol, (size_t)V.np));
+            F_TRY(falloc(c, &V.ooff, (size_t)V.nc + 1));
+            F_TRY(falloc(c, &V.oidx, (size_t)V.np));
+            F_TRY(cudaMemcpyAsync(V.pS, pS.data(), V.np * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.pcol, pcol.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.oidx, oidx.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+            size_t ncol = (size_t)343 * V.nmax;
+            if (c->split) {
+                F_TRY(falloc(c, &V.Bbuf32, ncol * P));
+                F_TRY(falloc(c, &V.Cbuf32, ncol * F.nblk * P));
+            } else {
+                F_TRY(falloc(c, &V.Bbuf, ncol * P));
+                F_TRY(falloc(c, &V.Cbuf, ncol * F.nblk * P));
+            }
+            F_TRY(cudaStreamSynchronize(c->s));
+        }
         double Tdt = V.T * c->P.dt;
         k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, V.s, V.hs, Tdt, c->P.dt, Tdt / 2.0, c->P.c,
                                                     V.op);
         F_TRY(cudaGetLastError());
+        if (c->split) {
+            // mixed form: FP32 operators for the emulated-FP32 tensor-core GEMM
+            F_TRY(falloc(c, &V.op32, nop));
+            k_to_float<<<152 * 32, 256, 0, c->s>>>((int64_t)nop, V.op, V.op32);
+            F_TRY(cudaGetLastError());
+            F_TRY(cudaStreamSynchronize(c->s));
+            auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)V.op);
+            if (it != c->allocs.end()) c->allocs.erase(it);
+            cudaFree(V.op);
+            V.op = nullptr;
+        }
         V.Tlen = c->P.c * Tdt;
     }
     return cudaStreamSynchronize(c->s);
@@ -644,11 +762,41 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
         int kl = (k + 1) / span - 1;
         FmmLevel &V = F.lev[l];
         const TreeLevel &T = c->tree.levels[l];
-        // M2L for source interval kl of this level
-        dim3 grid(V.nc, F.nblk);
-        k_m2l_apply<<<grid, 128, P * sizeof(double), s>>>(P, F.nblk, F.mu, l, V.nc, T.ckey, T.il, T.ilcount, V.M, V.op,
-                                                          V.ring, F.nslot, kl, V.G);
-        F_TRY(cudaGetLastError());
+        // M2L for source interval kl of this level: gather, one GEMM per
+        // offset, per-cell reduction into the locals (near future) and G
+        if (V.np > 0) {
+            const int R = F.nblk * P;
+            cudaEvent_t ev;
+            phase_begin(c, &ev);
+            const long long sA = (long long)R * P, sB = (long long)V.nmax * P, sC = (long long)V.nmax * R;
+            cublasStatus_t st;
+            if (c->split) {
+                // FP32 operands, FP32-accurate products on the BF16 tensor
+                // cores (three BF16 terms per operand), FP64 locals
+                k_m2l_gather<float><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf32);
+                const float one = 1.0f, zero = 0.0f;
+                st = cublasGemmStridedBatchedEx(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)V.nmax, P, &one, V.op32,
+                                                CUDA_R_32F, P, sA, V.Bbuf32, CUDA_R_32F, P, sB, &zero, V.Cbuf32,
+                                                CUDA_R_32F, R, sC, 343, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                                                CUBLAS_GEMM_DEFAULT);
+                k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf32,
+                                                         V.ring, V.G);
+            } else {
+                k_m2l_gather<double><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf);
+                const double one = 1.0, zero = 0.0;
+                st = cublasDgemmStridedBatched(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)V.nmax, P, &one, V.op, P, sA,
+                                               V.Bbuf, P, sB, &zero, V.Cbuf, R, sC, 343);
+                k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf,
+                                                          V.ring, V.G);
+            }
+            if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+            phase_end(c, PH_M2L, ev);
+            c->launches[PH_M2L] += 1;
+            c->m2l_flops += 2.0 * (double)R * P * (double)V.np;  // algorithmic (unpadded) flops
+            F_TRY(cudaGetLastError());
+        } else {
+            F_TRY(cudaMemsetAsync(V.G, 0, (size_t)d * V.nc * P * sizeof(double), s));
+        }
         double cm[16] = {0};
         cmp_table(d, kl, cm);
         F_TRY(cudaMemcpyAsync(F.cmp, cm, sizeof(cm), cudaMemcpyHostToDevice, s));
@@ -685,5 +833,11 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
 }
 
 #undef F_TRY
+
+void fmm_free(tdbem_ctx *c)
+{
+    if (c->fmm.blas) cublasDestroy(c->fmm.blas);
+    c->fmm.blas = nullptr;
+}
 
 }  // namespace tdbem

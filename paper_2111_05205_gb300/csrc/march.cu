@@ -64,7 +64,8 @@ __device__ __forceinline__ void df_renorm(DF &a)
 // coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
 // are read from their float-pair copies and the sum runs in double-float.
 template <bool HU, bool HW, bool SPLIT>
-__global__ void __launch_bounds__(kNearThreads) k_near_sum(int ns, int alpha, const int64_t *__restrict__ prow,
+__global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
+                                                              const int64_t *__restrict__ prow,
                                                            const int32_t *__restrict__ col,
                                                            const int64_t *__restrict__ rowblk,
                                                            const uint16_t *__restrict__ meta,
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_sum(int ns, int alpha, co
                                                            const double *__restrict__ far, double *b)
 {
     __shared__ double red[kNearThreads / 32];
+    if (alpha_dev) alpha = *alpha_dev;
     const int i = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -202,7 +204,7 @@ static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, c
     bool hu = c->d_ku != nullptr, hw = c->d_kw != nullptr;
     auto k = hu ? (hw ? k_near_sum<true, true, SPLIT> : k_near_sum<true, false, SPLIT>)
                 : (hw ? k_near_sum<false, true, SPLIT> : k_near_sum<false, false, SPLIT>);
-    k<<<c->ns, kNearThreads, 0, c->s>>>(c->ns, alpha, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
+    k<<<c->ns, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
                                        c->d_n, d_far, c->d_b);
     return cudaGetLastError();
@@ -257,11 +259,12 @@ cudaError_t launch_split_histories(tdbem_ctx *c)
 __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, const int32_t *__restrict__ acol,
                          const double *__restrict__ ainv, const double *__restrict__ b,
                          const double *__restrict__ xin, double *xout, int last, int64_t row,
-                         const int8_t *__restrict__ phi, double *u, double *q, float2 *us, float2 *qs,
-                         int *flag)
+                         const int *__restrict__ alpha_dev, const int8_t *__restrict__ phi, double *u, double *q,
+                         float2 *us, float2 *qs, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
+    if (alpha_dev) row = (int64_t)(*alpha_dev - 1) * ns;
     double s = b[i];
     if (xin) {
         for (int k = 0; k < width; ++k) {
@@ -287,8 +290,17 @@ cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last)
     double *xout = (it & 1) ? c->d_xb : c->d_xa;
     int64_t row = (int64_t)(alpha - 1) * c->ns;
     k_jacobi<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->ell_w, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, xout, last,
-                                                   row, c->d_phi, c->d_u, c->d_q, c->d_us, c->d_qs,
-                                                   c->d_flag);
+                                                   row, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_phi, c->d_u,
+                                                   c->d_q, c->d_us, c->d_qs, c->d_flag);
+    return cudaGetLastError();
+}
+
+// Advances the device-side step counter (graph-replayed steps).
+__global__ void k_alpha_next(int *alpha_dev) { *alpha_dev += 1; }
+
+cudaError_t launch_alpha_next(tdbem_ctx *c)
+{
+    k_alpha_next<<<1, 1, 0, c->s>>>(c->d_alpha);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,501 @@
+// Learned sparse approximate inverse (SAI) for the zero-lag system of
+// Eq. linear.  The paper only says the system is sparse and solved every
+// step; this component is an addition of this library.
+//
+// For row i of A (pattern: the diagonal and the off-diagonal entries of the
+// ELL store, at most W slots) a small network maps per-slot features to the
+// row of a left SAI M on the same pattern; the zero-lag solve then runs
+// preconditioned Richardson sweeps x <- x + M (b - A x) instead of Jacobi
+// sweeps (Jacobi is M = D^-1).  Features of slot k (k = 0: the diagonal;
+// then the off-diagonal entries by decreasing |A_ij|): A_ij / A_ii, the
+// distance |x_i - x_j| / (c dt) and a validity flag.  Network: in = 3W ->
+// hidden H (ReLU) -> W outputs o_k, M_ij = o_k / A_ii.  FP16 weights, FP32
+// arithmetic.  Training minimises sum_i || e_i^T - m_i^T A ||^2 over rows
+// of zero-lag matrices the method assembles, with hand-written forward,
+// backward and Adam kernels.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "tdbem_internal.cuh"
+
+namespace tdbem {
+
+constexpr int kSaiMaxW = 16;
+constexpr int kSaiMaxH = 64;
+
+struct SaiRow {
+    int n;                 // valid slots (diagonal first)
+    int col[kSaiMaxW];
+    float feat[3 * kSaiMaxW];
+    double inv_diag;
+};
+
+// Slots of row i in the canonical order: the diagonal, then off-diagonal
+// entries by decreasing magnitude (ties by column).
+__device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, const int32_t *acol,
+                        const double *ainv, const double *xc, double cdt, SaiRow &R)
+{
+    double ad = 1.0 / ainv[i];
+    int cols[kSaiMaxW];
+    double vals[kSaiMaxW];
+    int n = 0;
+    cols[n] = i;
+    vals[n++] = ad;
+    for (int k = 0; k < ell_w && n < W; ++k) {
+        int j = acol[(int64_t)k * ns + i];
+        if (j < 0) continue;
+        double v = aoff[(int64_t)k * ns + i];
+        int p = n++;
+        while (p > 1 && (fabs(vals[p - 1]) < fabs(v) || (fabs(vals[p - 1]) == fabs(v) && cols[p - 1] > j))) {
+            vals[p] = vals[p - 1];
+            cols[p] = cols[p - 1];
+            --p;
+        }
+        vals[p] = v;
+        cols[p] = j;
+    }
+    R.n = n;
+    R.inv_diag = ainv[i];
+    for (int k = 0; k < W; ++k) {
+        bool ok = k < n;
+        R.col[k] = ok ? cols[k] : -1;
+        double dx = 0, dy = 0, dz = 0;
+        if (ok) {
+            dx = xc[3 * i] - xc[3 * cols[k]];
+            dy = xc[3 * i + 1] - xc[3 * cols[k] + 1];
+            dz = xc[3 * i + 2] - xc[3 * cols[k] + 2];
+        }
+        R.feat[3 * k] = ok ? (float)(vals[k] * ainv[i]) : 0.f;
+        R.feat[3 * k + 1] = ok ? (float)(sqrt(dx * dx + dy * dy + dz * dz) / cdt) : 0.f;
+        R.feat[3 * k + 2] = ok ? 1.f : 0.f;
+    }
+}
+
+// Forward pass of one row: hidden activations h and outputs o.
+__device__ void sai_forward(int W, int H, const __half *w1, const __half *b1, const __half *w2, const __half *b2,
+                            const float *in, float *h, float *o)
+{
+    const int F = 3 * W;
+    for (int a = 0; a < H; ++a) {
+        float s = __half2float(b1[a]);
+        for (int f = 0; f < F; ++f) s += __half2float(w1[a * F + f]) * in[f];
+        h[a] = s > 0.f ? s : 0.f;
+    }
+    for (int k = 0; k < W; ++k) {
+        float s = __half2float(b2[k]);
+        for (int a = 0; a < H; ++a) s += __half2float(w2[k * H + a]) * h[a];
+        o[k] = s;
+    }
+}
+
+// Entry A_jl (l any column) from the ELL store.
+__device__ __forceinline__ double a_entry(int j, int l, int ns, int ell_w, const double *aoff, const int32_t *acol,
+                                          const double *ainv)
+{
+    if (j == l) return 1.0 / ainv[j];
+    for (int k = 0; k < ell_w; ++k)
+        if (acol[(int64_t)k * ns + j] == l) return aoff[(int64_t)k * ns + j];
+    return 0.0;
+}
+
+// One training pass over the rows of one matrix: loss of every row and the
+// gradients of the weights (FP32, accumulated with atomics).  Residual of
+// row i: r_l = sum_k M_{i,j_k} A_{j_k, l} - delta_il over the columns l of
+// the rows j_k.
+__global__ void k_sai_train_rows(int ns, int ell_w, int W, int H, const double *__restrict__ aoff,
+                                 const int32_t *__restrict__ acol, const double *__restrict__ ainv,
+                                 const double *__restrict__ xc, double cdt, const __half *__restrict__ w16,
+                                 float *grad, float *loss)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const int F = 3 * W;
+    const __half *w1 = w16, *b1 = w1 + H * F, *w2 = b1 + H, *b2 = w2 + W * H;
+    float *g1 = grad, *gb1 = g1 + H * F, *g2 = gb1 + H, *gb2 = g2 + W * H;
+    SaiRow R;
+    sai_row(i, ns, ell_w, W, aoff, acol, ainv, xc, cdt, R);
+    float h[kSaiMaxH], o[kSaiMaxW];
+    sai_forward(W, H, w1, b1, w2, b2, R.feat, h, o);
+    // residual over the union of the columns of rows j_k
+    int lc[kSaiMaxW * (kSaiMaxW + 1)];
+    double lv[kSaiMaxW * (kSaiMaxW + 1)];
+    int nl = 0;
+    auto add = [&](int l, double v) {
+        for (int t = 0; t < nl; ++t)
+            if (lc[t] == l) {
+                lv[t] += v;
+                return;
+            }
+        lc[nl] = l;
+        lv[nl++] = v;
+    };
+    add(i, -1.0);
+    for (int k = 0; k < R.n; ++k) {
+        int j = R.col[k];
+        double m = o[k] * R.inv_diag;
+        add(j, m / ainv[j]);
+        for (int e = 0; e < ell_w; ++e) {
+            int l = acol[(int64_t)e * ns + j];
+            if (l >= 0) add(l, m * aoff[(int64_t)e * ns + j]);
+        }
+    }
+    double L = 0.0;
+    for (int t = 0; t < nl; ++t) L += lv[t] * lv[t];
+    atomicAdd(loss, (float)L);
+    // dL/do_k = 2 sum_l r_l A_{j_k, l} / A_ii
+    float go[kSaiMaxW];
+    for (int k = 0; k < W; ++k) {
+        go[k] = 0.f;
+        if (k >= R.n) continue;
+        double s = 0.0;
+        for (int t = 0; t < nl; ++t) s += lv[t] * a_entry(R.col[k], lc[t], ns, ell_w, aoff, acol, ainv);
+        go[k] = (float)(2.0 * s * R.inv_diag);
+    }
+    for (int k = 0; k < W; ++k) {
+        if (go[k] == 0.f) continue;
+        atomicAdd(&gb2[k], go[k]);
+        for (int a = 0; a < H; ++a)
+            if (h[a] != 0.f) atomicAdd(&g2[k * H + a], go[k] * h[a]);
+    }
+    for (int a = 0; a < H; ++a) {
+        if (h[a] <= 0.f) continue;
+        float gh = 0.f;
+        for (int k = 0; k < W; ++k) gh += __half2float(w2[k * H + a]) * go[k];
+        if (gh == 0.f) continue;
+        atomicAdd(&gb1[a], gh);
+        for (int f = 0; f < F; ++f)
+            if (R.feat[f] != 0.f) atomicAdd(&g1[a * F + f], gh * R.feat[f]);
+    }
+}
+
+// Adam on the FP32 master weights; FP16 copies for the forward pass.
+__global__ void k_sai_adam(int n, float *w, float *m, float *v, const float *grad, float scale, float lr, float b1,
+                           float b2, float eps, int t, __half *w16)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float g = grad[e] * scale;
+    m[e] = b1 * m[e] + (1.f - b1) * g;
+    v[e] = b2 * v[e] + (1.f - b2) * g * g;
+    float mh = m[e] / (1.f - powf(b1, (float)t)), vh = v[e] / (1.f - powf(b2, (float)t));
+    w[e] -= lr * mh / (sqrtf(vh) + eps);
+    w16[e] = __float2half(w[e]);
+}
+
+// M of a context on the pattern of A (ELL store: [W][ns] values, columns).
+__global__ void k_sai_apply_net(int ns, int ell_w, int W, int H, const double *__restrict__ aoff,
+                                const int32_t *__restrict__ acol, const double *__restrict__ ainv,
+                                const double *__restrict__ xc, double cdt, const __half *__restrict__ w16, double *mval,
+                                int32_t *mcol)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const int F = 3 * W;
+    const __half *w1 = w16, *b1 = w1 + H * F, *w2 = b1 + H, *b2 = w2 + W * H;
+    SaiRow R;
+    sai_row(i, ns, ell_w, W, aoff, acol, ainv, xc, cdt, R);
+    float h[kSaiMaxH], o[kSaiMaxW];
+    sai_forward(W, H, w1, b1, w2, b2, R.feat, h, o);
+    for (int k = 0; k < W; ++k) {
+        mval[(int64_t)k * ns + i] = (k < R.n) ? (double)o[k] * R.inv_diag : 0.0;
+        mcol[(int64_t)k * ns + i] = R.col[k];
+    }
+}
+
+// Residual r = b - A x (x == nullptr: r = b).
+__global__ void k_residual(int ns, int ell_w, const double *__restrict__ aoff, const int32_t *__restrict__ acol,
+                           const double *__restrict__ ainv, const double *__restrict__ b,
+                           const double *__restrict__ x, double *r)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    double s = b[i];
+    if (x) {
+        s -= x[i] / ainv[i];
+        for (int k = 0; k < ell_w; ++k) {
+            int j = acol[(int64_t)k * ns + i];
+            if (j >= 0) s -= aoff[(int64_t)k * ns + i] * x[j];
+        }
+    }
+    r[i] = s;
+}
+
+// x' = x + M r (x == nullptr: x' = M r); the last sweep adds x' to the
+// unknown component of step a-1 (as the Jacobi sweep does).
+__global__ void k_sai_update(int ns, int W, const double *__restrict__ mval, const int32_t *__restrict__ mcol,
+                             const double *__restrict__ r, const double *__restrict__ x, double *xout, int last,
+                             int64_t row, const int8_t *__restrict__ phi, double *u, double *q, float2 *us,
+                             float2 *qs, int *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    double s = x ? x[i] : 0.0;
+    for (int k = 0; k < W; ++k) {
+        int j = mcol[(int64_t)k * ns + i];
+        if (j >= 0) s += mval[(int64_t)k * ns + i] * r[j];
+    }
+    if (last) {
+        double *hh = phi[i] ? u : q;
+        double v = hh[row + i] + s;
+        hh[row + i] = v;
+        if (us) {
+            float hi = __double2float_rn(v);
+            (phi[i] ? us : qs)[row + i] = make_float2(hi, __double2float_rn(v - (double)hi));
+        }
+        if (!isfinite(s)) atomicOr(flag, 1);
+    } else {
+        xout[i] = s;
+    }
+}
+
+}  // namespace tdbem
+
+struct tdbem_sai {
+    int W = 0, H = 0, nw = 0, t = 0;
+    float *w = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
+    __half *w16 = nullptr;
+    std::string err;
+};
+
+using namespace tdbem;
+
+namespace {
+
+int sai_fail(tdbem_sai *S, int code, const std::string &m)
+{
+    if (S) S->err = m;
+    return code;
+}
+
+// Deterministic weight initialisation (splitmix64 -> uniform +-sqrt(6/(fan_in+fan_out))).
+uint64_t splitmix(uint64_t &x)
+{
+    uint64_t z = (x += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdbem_sai_create(int32_t width, int32_t hidden, uint64_t seed, tdbem_sai **out)
+{
+    if (!out || width < 2 || width > kSaiMaxW || hidden < 1 || hidden > kSaiMaxH) return TDBEM_ERR_ARG;
+    tdbem_sai *S = new tdbem_sai();
+    S->W = width;
+    S->H = hidden;
+    const int F = 3 * width;
+    S->nw = hidden * F + hidden + width * hidden + width;
+    std::vector<float> w(S->nw, 0.f);
+    uint64_t st = seed;
+    float a1 = sqrtf(6.f / (F + hidden)), a2 = sqrtf(6.f / (hidden + width));
+    for (int e = 0; e < hidden * F; ++e) w[e] = a1 * (2.f * (float)((splitmix(st) >> 11) * 0x1.0p-53) - 1.f);
+    for (int e = 0; e < width * hidden; ++e)
+        w[hidden * F + hidden + e] = a2 * (2.f * (float)((splitmix(st) >> 11) * 0x1.0p-53) - 1.f);
+    // start from Jacobi: the output of the diagonal slot biased to 1 (M_ii = 1/A_ii)
+    w[hidden * F + hidden + width * hidden + 0] = 1.f;
+    std::vector<__half> w16(S->nw);
+    for (int e = 0; e < S->nw; ++e) w16[e] = __float2half(w[e]);
+    bool ok = cudaMalloc(&S->w, S->nw * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&S->m, S->nw * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&S->v, S->nw * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&S->grad, S->nw * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&S->loss, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&S->w16, S->nw * sizeof(__half)) == cudaSuccess;
+    if (ok) {
+        cudaMemcpy(S->w, w.data(), S->nw * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(S->w16, w16.data(), S->nw * sizeof(__half), cudaMemcpyHostToDevice);
+        cudaMemset(S->m, 0, S->nw * sizeof(float));
+        cudaMemset(S->v, 0, S->nw * sizeof(float));
+    }
+    if (!ok) {
+        tdbem_sai_destroy(S);
+        return TDBEM_ERR_OOM;
+    }
+    *out = S;
+    return TDBEM_OK;
+}
+
+void tdbem_sai_destroy(tdbem_sai *S)
+{
+    if (!S) return;
+    cudaFree(S->w);
+    cudaFree(S->m);
+    cudaFree(S->v);
+    cudaFree(S->grad);
+    cudaFree(S->loss);
+    cudaFree(S->w16);
+    delete S;
+}
+
+const char *tdbem_sai_last_error(const tdbem_sai *S) { return S ? S->err.c_str() : "null trainer"; }
+
+int tdbem_sai_weights(tdbem_sai *S, float *inout, int64_t *count, int32_t set)
+{
+    if (!S || !count) return TDBEM_ERR_ARG;
+    *count = S->nw;
+    if (!inout) return TDBEM_OK;
+    if (set) {
+        std::vector<__half> w16(S->nw);
+        for (int e = 0; e < S->nw; ++e) w16[e] = __float2half(inout[e]);
+        if (cudaMemcpy(S->w, inout, S->nw * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(S->w16, w16.data(), S->nw * sizeof(__half), cudaMemcpyHostToDevice) != cudaSuccess)
+            return sai_fail(S, TDBEM_ERR_CUDA, "weight upload");
+        cudaMemset(S->m, 0, S->nw * sizeof(float));
+        cudaMemset(S->v, 0, S->nw * sizeof(float));
+        S->t = 0;
+    } else {
+        // the FP16 weights the network computes with, as floats
+        std::vector<__half> w16(S->nw);
+        if (cudaMemcpy(w16.data(), S->w16, S->nw * sizeof(__half), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return sai_fail(S, TDBEM_ERR_CUDA, "weight download");
+        for (int e = 0; e < S->nw; ++e) inout[e] = __half2float(w16[e]);
+    }
+    return TDBEM_OK;
+}
+
+static int sai_pass(tdbem_sai *S, tdbem_ctx *c, float *loss_host)
+{
+    if (!c || !c->prepared || !c->d_aoff) return sai_fail(S, TDBEM_ERR_STATE, "context not prepared");
+    cudaMemsetAsync(S->grad, 0, S->nw * sizeof(float), c->s);
+    cudaMemsetAsync(S->loss, 0, sizeof(float), c->s);
+    k_sai_train_rows<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->ell_w, S->W, S->H, c->d_aoff, c->d_acol,
+                                                            c->d_ainv, c->d_xc, c->cdt, S->w16, S->grad, S->loss);
+    if (cudaGetLastError() != cudaSuccess) return sai_fail(S, TDBEM_ERR_CUDA, "training kernel");
+    if (loss_host) cudaMemcpyAsync(loss_host, S->loss, sizeof(float), cudaMemcpyDeviceToHost, c->s);
+    return TDBEM_OK;
+}
+
+// Loss and gradient of one context's rows at the current weights (no update).
+int tdbem_sai_gradient(tdbem_sai *S, tdbem_ctx *c, float *grad, float *loss)
+{
+    if (!S || !grad || !loss) return TDBEM_ERR_ARG;
+    int r = sai_pass(S, c, loss);
+    if (r != TDBEM_OK) return r;
+    if (cudaMemcpyAsync(grad, S->grad, S->nw * sizeof(float), cudaMemcpyDeviceToHost, c->s) != cudaSuccess ||
+        cudaStreamSynchronize(c->s) != cudaSuccess)
+        return sai_fail(S, TDBEM_ERR_CUDA, "gradient download");
+    return TDBEM_OK;
+}
+
+// Adam over the contexts' rows for `epochs` passes (one update per context
+// and pass, gradient scaled by 1/ns); loss_out: mean row loss of the last pass.
+int tdbem_sai_train(tdbem_sai *S, tdbem_ctx *const *ctxs, int32_t n, int32_t epochs, float lr, float *loss_out)
+{
+    if (!S || !ctxs || n < 1 || epochs < 1) return TDBEM_ERR_ARG;
+    double tot = 0.0;
+    int64_t rows = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        tot = 0.0;
+        rows = 0;
+        for (int k = 0; k < n; ++k) {
+            tdbem_ctx *c = ctxs[k];
+            float L = 0.f;
+            int r = sai_pass(S, c, &L);
+            if (r != TDBEM_OK) return r;
+            S->t += 1;
+            k_sai_adam<<<(S->nw + 255) / 256, 256, 0, c->s>>>(S->nw, S->w, S->m, S->v, S->grad, 1.f / c->ns, lr,
+                                                              0.9f, 0.999f, 1e-8f, S->t, S->w16);
+            if (cudaStreamSynchronize(c->s) != cudaSuccess) return sai_fail(S, TDBEM_ERR_CUDA, "training step");
+            tot += L;
+            rows += c->ns;
+        }
+    }
+    if (loss_out) *loss_out = (float)(tot / rows);
+    return TDBEM_OK;
+}
+
+// Installs the learned M as the zero-lag solver of a context when its
+// a-priori sweep count (||I - M A||_inf = q': error <= q'^K) needs fewer
+// kernel launches than Jacobi's; otherwise Jacobi stays (the fallback).
+// *sweeps receives the sweeps of the solver in use, *contraction its q.
+int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_t *sweeps, double *contraction)
+{
+    if (!c || !S) return TDBEM_ERR_ARG;
+    if (!c->prepared) return TDBEM_ERR_STATE;
+    const int ns = c->ns, W = S->W, E = c->ell_w;
+    double *mval = nullptr;
+    int32_t *mcol = nullptr;
+    if (cudaMalloc(&mval, (size_t)W * ns * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&mcol, (size_t)W * ns * sizeof(int32_t)) != cudaSuccess)
+        return TDBEM_ERR_OOM;
+    c->allocs.push_back(mval);
+    c->allocs.push_back(mcol);
+    k_sai_apply_net<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, E, W, S->H, c->d_aoff, c->d_acol, c->d_ainv, c->d_xc,
+                                                         c->cdt, S->w16, mval, mcol);
+    std::vector<double> mv((size_t)W * ns), av((size_t)E * ns), ai(ns);
+    std::vector<int32_t> mc((size_t)W * ns), ac((size_t)E * ns);
+    cudaMemcpyAsync(mv.data(), mval, mv.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(mc.data(), mcol, mc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(av.data(), c->d_aoff, av.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(ac.data(), c->d_acol, ac.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(ai.data(), c->d_ainv, ai.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return TDBEM_ERR_CUDA;
+    // q' = max_i sum_l |delta_il - (M A)_il|
+    double qmax = 0.0;
+    std::vector<std::pair<int, double>> acc;
+    for (int i = 0; i < ns; ++i) {
+        acc.clear();
+        auto add = [&](int l, double v) {
+            for (auto &p : acc)
+                if (p.first == l) {
+                    p.second += v;
+                    return;
+                }
+            acc.push_back({l, v});
+        };
+        add(i, -1.0);
+        for (int k = 0; k < W; ++k) {
+            int j = mc[(size_t)k * ns + i];
+            if (j < 0) continue;
+            double m = mv[(size_t)k * ns + i];
+            add(j, m / ai[j]);
+            for (int e = 0; e < E; ++e) {
+                int l = ac[(size_t)e * ns + j];
+                if (l >= 0) add(l, m * av[(size_t)e * ns + j]);
+            }
+        }
+        double s = 0.0;
+        for (auto &p : acc) s += fabs(p.second);
+        qmax = std::max(qmax, s);
+    }
+    double tol = c->P.solver_tol > 0 ? c->P.solver_tol : 1e-16;
+    int K = (qmax > 0.0 && qmax < 1.0) ? std::max(1, (int)ceil(log(tol) / log(qmax))) : 1 << 30;
+    // a preconditioned sweep is two launches (residual, update); the first is one
+    bool better = qmax < 1.0 && (2 * K - 1) < c->solve_iters;
+    if (better) {
+        c->sai_val = mval;
+        c->sai_col = mcol;
+        c->sai_w = W;
+        c->sai_iters = K;
+        c->sai_contraction = qmax;
+    }
+    if (use_sai) *use_sai = better ? 1 : 0;
+    if (sweeps) *sweeps = better ? K : c->solve_iters;
+    if (contraction) *contraction = qmax;
+    return TDBEM_OK;
+}
+
+}  // extern "C"
+
+namespace tdbem {
+
+// The SAI-preconditioned zero-lag solve of one step (sweep it of K).
+cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it)
+{
+    const int ns = c->ns;
+    const bool last = (it == c->sai_iters - 1);
+    const double *xin = (it == 0) ? nullptr : ((it & 1) ? c->d_xa : c->d_xb);
+    double *xout = (it & 1) ? c->d_xb : c->d_xa;
+    double *r = c->d_r;
+    k_residual<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->ell_w, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, r);
+    int64_t row = (int64_t)(alpha - 1) * ns;
+    k_sai_update<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->sai_w, c->sai_val, c->sai_col, r, xin, xout, last, row,
+                                                     c->d_phi, c->d_u, c->d_q, c->d_us, c->d_qs, c->d_flag);
+    return cudaGetLastError();
+}
+
+}  // namespace tdbem

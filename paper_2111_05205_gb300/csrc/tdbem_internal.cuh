@@ -60,10 +60,25 @@ struct FmmLevel {
     double *G = nullptr;         // [d][nc][P] contributions L^(p)_{k+mu+1,k}
     double *op = nullptr;        // [343][mu+1+d][P][P] M2L operators
     double *Sm = nullptr;        // [2][ps][ps] transfer to the parent level
+    // interaction pairs grouped by offset for the GEMM form of the M2L
+    int64_t np = 0;              // pairs
+    std::vector<int64_t> ostart; // [344] first pair of each offset
+    int32_t *pS = nullptr;       // [np] source cell of each pair
+    int64_t nmax = 0;            // columns per offset slab (the busiest offset's pairs)
+    int64_t *pcol = nullptr;     // [np] padded column of each pair
+    int64_t *ooff = nullptr;     // [nc+1] pairs of each observation cell (CSR)
+    int64_t *oidx = nullptr;     // [np] their padded columns
+    double *Bbuf = nullptr;      // [np][P] gathered moments
+    double *Cbuf = nullptr;      // [np][(mu+1+d) P] operator stack x moment
+    float *op32 = nullptr;       // mixed form: FP32 operators, operands and products
+    float *Bbuf32 = nullptr;
+    float *Cbuf32 = nullptr;
+    int64_t flops_per_interval = 0;  // 2 (mu+1+d) P^2 x pairs
 };
 
 struct Fmm {
     bool on = false;
+    struct cublasContext *blas = nullptr;  // cuBLAS handle
     int L = 0, ps = 0, pt = 0, P3 = 0, P = 0, mu = 0, Lt = 0, nblk = 0, nd = 0, nslot = 0;
     double rho = 0;
     std::vector<FmmLevel> lev;
@@ -81,7 +96,7 @@ struct Pending {
     cudaEvent_t a, b;
 };
 
-enum { PH_RHS = 0, PH_NEAR = 1, PH_SOLVE = 2, PH_FAR = 3, PH_COUNT = 4 };
+enum { PH_RHS = 0, PH_NEAR = 1, PH_SOLVE = 2, PH_FAR = 3, PH_M2L = 4, PH_COUNT = 5 };
 
 struct Status {
     int code = TDBEM_OK;
@@ -127,7 +142,7 @@ struct tdbem_ctx {
     int64_t nbt = 0;             // blocks in total
     uint16_t *d_meta = nullptr;  // [npairs] lag windows
     int32_t *d_btot = nullptr;   // [nbt] coefficients per 32-pair block
-    int64_t *d_boff = nullptr;   // [nbt] first coefficient of each block
+    int64_t *d_boff = nullptr;   // [nbt+1] first coefficient of each block (last: ncoef)
     int smax = 0;                // largest window length
     int gmax = 0;                // largest lag stored
     int64_t npairs = 0, ncoef = 0;
@@ -148,6 +163,15 @@ struct tdbem_ctx {
     double *d_xout = nullptr;
     int xout_cap = 0;
     int *d_flag = nullptr;       // device error flags
+    // learned SAI for the zero-lag solve (nullptr: Jacobi)
+    double *sai_val = nullptr;   // [sai_w][ns]
+    int32_t *sai_col = nullptr;  // [sai_w][ns]
+    int sai_w = 0, sai_iters = 0;
+    double sai_contraction = 0.0;
+    double *d_r = nullptr;       // [ns] residual
+    int *d_alpha = nullptr;      // device-side step counter for graph-replayed steps
+    bool alpha_dev_on = false;   // kernels read the step from d_alpha (while capturing)
+    cudaGraphExec_t graph = nullptr;  // one captured step (direct path)
     std::vector<void *> allocs;  // every cudaMalloc of the context
 
     tdbem::Tree tree;  // built when P.depth > 0
@@ -156,8 +180,9 @@ struct tdbem_ctx {
     // timing
     std::vector<tdbem::Pending> pending;
     std::vector<cudaEvent_t> pool;
-    double ms[tdbem::PH_COUNT] = {0, 0, 0, 0};
-    int64_t launches[tdbem::PH_COUNT] = {0, 0, 0, 0};
+    double ms[tdbem::PH_COUNT] = {0, 0, 0, 0, 0};
+    int64_t launches[tdbem::PH_COUNT] = {0, 0, 0, 0, 0};
+    double m2l_flops = 0.0;  // algorithmic flops of the M2L GEMMs since the last reset
     int64_t steps_total = 0;
     double ms_prepare = 0.0;
 };
@@ -179,12 +204,18 @@ cudaError_t build_near_lists(tdbem_ctx *c);
 // Space-time FMM (fmm.cu)
 cudaError_t fmm_setup(tdbem_ctx *c, std::string &why);
 cudaError_t fmm_boundary(tdbem_ctx *c, int k);
+// Phase timer hooks for fmm.cu (events on the context's stream).
+void phase_begin(tdbem_ctx *c, cudaEvent_t *e);
+void phase_end(tdbem_ctx *c, int phase, cudaEvent_t e);
+void fmm_free(tdbem_ctx *c);
 void free_tree(tdbem_ctx *c);
 
 // Kernel launchers (march.cu)
 cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far);
 cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last);
 cudaError_t launch_gather_x(tdbem_ctx *c, int a0, int nsteps, double *x);
+cudaError_t launch_alpha_next(tdbem_ctx *c);
+cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it);
 cudaError_t launch_split_coefficients(tdbem_ctx *c);
 cudaError_t launch_split_histories(tdbem_ctx *c);
 

@@ -37,13 +37,21 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,L,p,nsteps", CASES)
-def test_fmm_far_field_matches_oracle(name, L, p, nsteps):
+def test_fmm_far_field_matches_oracle(name, L, p, nsteps, precision):
+    """precision 0: FP64 M2L, 1e-10.  precision 1 (mixed): FP32 operators and
+    moments with FP32-accurate tensor-core products (FP64 locals and
+    recurrence state), 1e-2 of the far field's scale: the tau-form far field
+    (Eq. target) is a sum whose terms are ~1e4-1e5 times larger than the
+    result (U grows like g^d while tau is a (d+1)-th difference), so FP32
+    rounding of the products (6e-8) shows up at ~3e-3 (measured on the
+    ellipsoid case)."""
     _need_gpu()
     from paper_2111_05205_gb300 import abi
     from tests.gpu_cases import gpu_solver
     w = workload(name, nt=nsteps + 2)
-    s = gpu_solver(w, depth=L, fmm=(p, p, 0))
+    s = gpu_solver(w, depth=L, fmm=(p, p, 0), precision=precision)
     try:
         st = s.stats()
         H = ofmm.Hierarchy(w.xyz, w.tri, L, w.c, w.dt, w.nt, p, p, w.d)
@@ -63,7 +71,8 @@ def test_fmm_far_field_matches_oracle(name, L, p, nsteps):
         got = far[:, rows]
         scale = np.abs(ref).max()
         assert scale > 0
-        assert np.abs(got - ref).max() <= 1e-10 * scale, (np.abs(got - ref).max(), scale)
+        tol = 1e-10 if precision == 0 else 1e-2
+        assert np.abs(got - ref).max() <= tol * scale, (np.abs(got - ref).max(), scale)
     finally:
         s.close()
 
