@@ -120,9 +120,24 @@ def _geometry(w):
     return xc, -g / np.linalg.norm(g, axis=1, keepdims=True)
 
 
+def _unknown(s, w, n):
+    u, q = s.solution(0, n)
+    return u if w.bc == "neumann" else q
+
+
+def _timed(abi, torch, ctx, nsteps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    abi.tdbem_step(ctx, nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def run_ours(args):
     import torch
-    from paper_2111_05205_gb300 import abi, build
+    from paper_2111_05205_gb300 import Solver, abi, build
     from synth import workload
 
     rank = int(os.environ.get("RANK", "0"))
@@ -136,40 +151,38 @@ def run_ours(args):
     build.build()
 
     w = workload(args.workload)
-    from paper_2111_05205_gb300 import Solver
-    # spin-up + warm-up + timed (device) + timed (e2e) steps must fit in Nt-1
-    probe_gmax = 260
-    need = probe_gmax + 2 * (args.warmup + args.steps) + 2
+    fmm = args.algo == "fmm"
+    spin = 260  # untimed steps before the warm-up: every lag window in use
+    need = spin + 2 * (args.warmup + args.steps) + 2
     w.nt = max(w.nt, need)
     stream = torch.cuda.current_stream().cuda_stream
-    t0 = time.time()
     phi = np.full(w.ns, 1 if w.bc == "neumann" else 0, np.int8)
-    s = Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi,
-               incident=(w.direction, w.t0, w.sigma), stream=stream, precision=args.precision)
+    inc = (w.direction, w.t0, w.sigma)
+
+    def make(precision, algo_fmm):
+        kw = dict(depth=args.depth, fmm=(args.ps, args.pt, 0)) if algo_fmm else {}
+        return Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi, incident=inc, stream=stream,
+                      precision=precision, **kw)
+
+    t0 = time.time()
+    s = make(args.precision, fmm)
     setup_s = time.time() - t0
     st0 = s.stats()
     gmax = st0["gamma_max"]
     ctx = s.ctx
-    # spin-up to steady state, then warm-up
-    abi.tdbem_step(ctx, gmax)
+    abi.tdbem_step(ctx, spin)
     abi.tdbem_step(ctx, args.warmup)
     abi.tdbem_sync(ctx)
     abi.tdbem_reset_stats(ctx)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")
-        ev0.record()
-        abi.tdbem_step(ctx, args.steps)
-        ev1.record()
-        torch.cuda.synchronize()
+        ms = _timed(abi, torch, ctx, args.steps)
         torch.cuda.nvtx.range_pop()
     if dist is not None:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     st = s.stats()
     abi.tdbem_sync(ctx)
     if dist is not None:
@@ -193,21 +206,14 @@ def run_ours(args):
         abi.tdbem_step_io(ctx, 1, exc[r], xout[r], on_device=False)
     e2e_s = time.perf_counter() - t_e
     assert np.isfinite(xout.numpy()).all()
+    n_done = abi.tdbem_steps_done(ctx)
+    X = _unknown(s, w, n_done)
+    s.close()
 
     hbm, peak_kind = _peaks()
     near_ms = st["ms_near"] / max(st["launches_near"], 1)
-    achieved = st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9
-    launches = (st["launches_near"] + st["launches_solve"]) 
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "near_sum_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            with open(tr_path) as f:
-                tr = json.load(f)
-            if tr.get("kernel_rev") == _kernel_rev():
-                traffic = tr["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    near_gbs = st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9
+    launches = st["launches_near"] + st["launches_solve"]
     out = {
         "metric": METRIC,
         "value": world * 1000.0 / ms_step,
@@ -219,35 +225,145 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+df32",
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": args.workload + "_direct_" + args.precision, "ns": w.ns,
-                   "precision": ("FP64 coefficients, histories, FMA and solve" if args.precision == "fp64" else
-                                 "FP64 coefficients and solve; history sum on FP32 pairs (48-bit) in "
-                                 "double-float arithmetic"), "d": w.d, "bie": w.bie, "bc": w.bc,
-                   "gamma_max": gmax, "spinup_steps": gmax, "coefficients_per_kind": st["n_coef"],
-                   "l2": "working set (%.1f GB per step) larger than L2; no flush" %
-                         (st["near_bytes_per_step"] / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single-gpu", "setup_s": round(setup_s, 2)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic, "kernel": "k_near_sum", "peak_source": peak_kind,
-                     "bytes_per_launch": st["near_bytes_per_step"], "avg_launch_ms": near_ms},
-        "phases_ms_per_step": {"near": near_ms, "solve": st["ms_solve"] / max(st["steps"], 1),
-                               "solve_sweeps": st["solve_iters"]},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "time-steps/s",
                 "h2d_bytes_per_step": w.ns * 8, "d2h_bytes_per_step": w.ns * 8},
-        "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
-    s.close()
-    if args.fp64_form and args.precision != "fp64":
-        out["fp64_form"] = fp64_form(args, w, phi, stream)
+    phases = {"near_ms": near_ms, "solve_ms": st["ms_solve"] / max(st["steps"], 1),
+              "solve_sweeps": st["solve_iters"]}
+    if fmm:
+        bf16, bf_kind = _bf16_peak()
+        emu = 9.0  # FP32 products emulated by nine BF16 products
+        peak = bf16 / emu if args.precision != "fp64" else FP64_TFLOPS
+        m2l_tf = st["m2l_flops"] / (st["ms_m2l"] * 1e-3) / 1e12 if st["ms_m2l"] > 0 else 0.0
+        phases.update({"far_ms": st["ms_far"] / args.steps, "m2l_ms": st["ms_m2l"] / args.steps,
+                       "m2l_tflops": m2l_tf, "Lt": st["fmm_lt"], "mu": st["fmm_mu"]})
+        launches += st["launches_far"] * 8 + st["launches_m2l"] * 3
+        out["config"] = {"workload": args.workload + "_fmm_L%d_p%dx%d_%s" % (args.depth, args.ps, args.pt,
+                                                                              args.precision),
+                         "ns": w.ns, "d": w.d, "bie": w.bie, "bc": w.bc, "depth": args.depth, "ps": args.ps,
+                         "pt": args.pt, "mu": st["fmm_mu"], "Lt": st["fmm_lt"],
+                         "precision": ("FP64 throughout" if args.precision == "fp64" else
+                                       "M2L FP32 on tensor cores (cuBLAS BF16x9 emulation), FP64 locals and "
+                                       "recurrence, near-field history sum on FP32 pairs in double-float, FP64 "
+                                       "coefficients and solve"),
+                         "l2": "near coefficients + operator bank read every step exceed the 129 MB L2 only "
+                               "partly; no flush", "setup_s": round(setup_s, 2),
+                         "parallelism": "replicas" if world > 1 else "single-gpu"}
+        out["roofline"] = {"bound": "tensor", "achieved": m2l_tf, "peak": peak, "unit": "TFLOP/s",
+                           "frac": m2l_tf / peak, "traffic": None, "kernel": "M2L GEMM (cuBLAS, all offsets)",
+                           "peak_source": ("measured bf16 / 9" if args.precision != "fp64" else
+                                           "FP64 FMA probe (measured)"), "flops_per_step": st["m2l_flops"] / args.steps}
+        out["near_roofline"] = {"bound": "hbm", "achieved": near_gbs, "peak": hbm, "frac": near_gbs / hbm}
+    else:
+        out["config"] = {"workload": args.workload + "_direct_" + args.precision, "ns": w.ns, "d": w.d,
+                         "bie": w.bie, "bc": w.bc, "gamma_max": gmax, "spinup_steps": spin,
+                         "coefficients_per_kind": st["n_coef"],
+                         "precision": ("FP64 coefficients, histories, FMA and solve" if args.precision == "fp64" else
+                                       "FP64 coefficients and solve; history sum on FP32 pairs (48-bit) in "
+                                       "double-float arithmetic"),
+                         "l2": "working set (%.1f GB per step) larger than L2; no flush" %
+                               (st["near_bytes_per_step"] / 1e9),
+                         "parallelism": "replicas" if world > 1 else "single-gpu", "setup_s": round(setup_s, 2)}
+        out["roofline"] = {"bound": "hbm", "achieved": near_gbs, "peak": hbm, "unit": "GB/s", "frac": near_gbs / hbm,
+                           "traffic": _traffic(st), "kernel": "k_near_sum", "peak_source": peak_kind,
+                           "bytes_per_launch": st["near_bytes_per_step"], "avg_launch_ms": near_ms}
+    out["phases_ms_per_step"] = phases
+    out["gpu_launches"] = int(launches)
+
+    if fmm:
+        # accuracy: the direct path (parity-checked against the FP64 oracle)
+        # over the same steps, and the FMM's FP64 form
+        d = make("split", False)
+        abi.tdbem_step(d.ctx, spin)
+        Xd = _unknown(d, w, spin)
+        d.close()
+        X = X[:spin]
+        out["accuracy"] = {"rel_l2_vs_direct": float(np.linalg.norm(X - Xd) / np.linalg.norm(Xd)),
+                           "steps": spin, "target": 1e-3,
+                           "reference": "direct history sum, parity 1e-11 with the FP64 oracle"}
+        if args.fp64_form and args.precision != "fp64":
+            f64 = make("fp64", True)
+            abi.tdbem_step(f64.ctx, spin)
+            Xf = _unknown(f64, w, spin)
+            abi.tdbem_reset_stats(f64.ctx)
+            msf = _timed(abi, torch, f64.ctx, min(args.steps, 40))
+            f64.close()
+            out["fp64_form"] = {"value": 1000.0 * min(args.steps, 40) / msf, "unit": "time-steps/s",
+                                "rel_l2_vs_direct": float(np.linalg.norm(Xf - Xd) / np.linalg.norm(Xd))}
+        if args.direct_form:
+            dd = make("split", False)
+            abi.tdbem_step(dd.ctx, spin)
+            msd = _timed(abi, torch, dd.ctx, args.steps)
+            dd.close()
+            out["direct_form"] = {"value": 1000.0 * args.steps / msd, "unit": "time-steps/s",
+                                  "precision": "split", "note": "exact path (no FMM), all element pairs"}
+    else:
+        if args.fp64_form and args.precision != "fp64":
+            out["fp64_form"] = fp64_form(args, w, phi, stream)
+        if args.fmm_form:
+            # the space-time FMM (mixed form) on the same workload and steps:
+            # throughput and its error against this direct history
+            t1 = time.time()
+            f = make(args.precision, True)
+            fsetup = time.time() - t1
+            abi.tdbem_step(f.ctx, spin + args.warmup)
+            abi.tdbem_sync(f.ctx)
+            abi.tdbem_reset_stats(f.ctx)
+            msf = _timed(abi, torch, f.ctx, args.steps)
+            stf = f.stats()
+            rest = n_done - abi.tdbem_steps_done(f.ctx)
+            if rest > 0:
+                abi.tdbem_step(f.ctx, rest)
+            Xf = _unknown(f, w, n_done)
+            f.close()
+            m2l_tf = stf["m2l_flops"] / (stf["ms_m2l"] * 1e-3) / 1e12 if stf["ms_m2l"] > 0 else 0.0
+            err = [float(np.linalg.norm(Xf[:n] - X[:n]) / np.linalg.norm(X[:n])) for n in (60, 120, 240, n_done)
+                   if n <= n_done]
+            out["fmm_form"] = {"value": 1000.0 * args.steps / msf, "unit": "time-steps/s",
+                               "config": "depth %d, ps=pt=%d, mu=%d, Lt=%d, %s" % (
+                                   args.depth, args.ps, stf["fmm_mu"], stf["fmm_lt"],
+                                   "M2L FP32 on tensor cores (BF16x9)" if args.precision != "fp64" else "FP64"),
+                               "rel_l2_vs_direct_after_steps": dict(zip([str(n) for n in (60, 120, 240, n_done)
+                                                                         if n <= n_done], err)),
+                               "meets_1e-3": bool(max(err) <= 1e-3), "m2l_tflops": m2l_tf,
+                               "m2l_ms_per_step": stf["ms_m2l"] / args.steps,
+                               "near_ms_per_step": stf["ms_near"] / args.steps,
+                               "far_ms_per_step": stf["ms_far"] / args.steps, "setup_s": round(fsetup, 2)}
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, rows=args.cpu_rows)
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+FP64_TFLOPS = 1.19  # FP64 FMA-chain probe on this machine's GB300 (0.596 TFMA/s)
+
+
+def _traffic(st):
+    tr_path = os.path.join(ROOT, "profiles", "near_sum_traffic.json")
+    if not os.path.exists(tr_path):
+        return None
+    try:
+        with open(tr_path) as f:
+            tr = json.load(f)
+        if tr.get("kernel_rev") != _kernel_rev():
+            return None
+        return tr["bytes_per_algorithmic_byte"] * st["near_bytes_per_step"]
+    except Exception:
+        return None
 
 
 def fp64_form(args, w, phi, stream):
@@ -314,6 +430,59 @@ def cpu_baseline(w, rows=4, repeats=3):
                       % (rows, w.ns, gm, w.ns / rows)}
 
 
+def run_batch(args):
+    """Batched driver: N independent instances (seeded ellipsoids, Ns cycling
+    80 / 320 / 1280, d cycling 2 / 1, BMBIE, sound-hard, split precision),
+    each advanced `steps` steps by (a) plain launches, one instance after
+    another, (b) one graph per instance, (c) one graph for all instances."""
+    import torch
+    from paper_2111_05205_gb300 import abi, build
+    from synth import workload
+    from tests.gpu_cases import gpu_solver
+    build.build()
+    n, k = args.batch, args.steps
+    ws = [workload("ellipsoid%d_bmbie_d%d_hard_plane_s%d" % ((80, 320, 1280)[i % 3], 1 if i % 2 else 2, i + 1),
+                   nt=3 * k + args.warmup + 3) for i in range(n)]
+    sols = [gpu_solver(w, precision=1) for w in ws]
+    try:
+        for s in sols:
+            abi.tdbem_step(s.ctx, args.warmup)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for s in sols:
+            abi.tdbem_step(s.ctx, k)
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t
+        for s in sols:
+            abi.tdbem_step_graph(s.ctx, 1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for s in sols:
+            abi.tdbem_step_graph(s.ctx, k - 1)
+        torch.cuda.synchronize()
+        t_graph = (time.perf_counter() - t) * k / (k - 1)
+        B = abi.tdbem_batch_create([s.ctx for s in sols])
+        try:
+            abi.tdbem_batch_step(B, 1)
+            abi.tdbem_batch_sync(B)
+            t = time.perf_counter()
+            abi.tdbem_batch_step(B, k - 1)
+            abi.tdbem_batch_sync(B)
+            t_batch = (time.perf_counter() - t) * k / (k - 1)
+        finally:
+            abi.tdbem_batch_destroy(B)
+    finally:
+        for s in sols:
+            s.close()
+    tot = n * k
+    print(json.dumps({"metric": "instance-steps/sec, batched driver", "value": tot / t_batch,
+                      "unit": "instance-steps/s", "n_gpus": 1, "steps": k, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "f64+df32", "data": "synthetic",
+                      "config": {"workload": "batch%d_ellipsoids_ns80-320-1280_bmbie_d1-2" % n, "instances": n},
+                      "plain_launches": tot / t_plain, "graph_per_instance": tot / t_graph,
+                      "timing": "host clock around each mode, device synchronised"}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -349,11 +518,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"])
     ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false")
+    ap.add_argument("--algo", default="direct", choices=["direct", "fmm"])
+    ap.add_argument("--depth", type=int, default=4)
+    ap.add_argument("--ps", type=int, default=4)
+    ap.add_argument("--pt", type=int, default=4)
+    ap.add_argument("--direct-form", action="store_true")
+    ap.add_argument("--no-fmm-form", dest="fmm_form", action="store_false")
+    ap.add_argument("--batch", type=int, default=0, help="measure the batched driver with N instances")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -190,11 +190,12 @@ const char *tdbem_batch_last_error(const tdbem_batch *batch);
 
 /* Learned sparse approximate inverse for the zero-lag solve (an addition
  * of this library; the paper only states that the system is sparse).  A
- * trainer holds a 2-layer network (3*width inputs -> hidden ReLU -> width
+ * trainer holds a 2-layer network (5*width inputs -> hidden ReLU -> width
  * outputs, FP16 weights, FP32 arithmetic) that maps the features of row i
- * of A (per slot k, the diagonal first and then the off-diagonal entries by
- * decreasing |A_ij|: A_ij/A_ii, |x_i - x_j|/(c dt), 1) to the row of a
- * left SAI M on A's pattern (M_ij = output_k / A_ii).  Training minimises
+ * of A (per slot k, the diagonal first and then the off-diagonal entries
+ * with |A_ij| >= 1e-12 |A_ii| by decreasing |A_ij|: A_ij/A_ii, A_jj/A_ii,
+ * A_ji/A_ii, |x_i - x_j|/(c dt), 1) to the row of a left SAI M on that
+ * pattern (M_ij = output_k / A_ii).  Training minimises
  * sum_i ||e_i^T - m_i^T A||^2 over the rows of prepared contexts (their
  * zero-lag matrices; a context with nt = 2 computes only those) with Adam,
  * one update per context and pass, all on the GPU.  width 2..16, hidden
@@ -210,10 +211,22 @@ int tdbem_sai_gradient(tdbem_sai *sai, tdbem_ctx *ctx, float *grad, float *loss)
  * floats) to inout, set = 1 loads inout (and resets the optimiser). */
 int tdbem_sai_weights(tdbem_sai *sai, float *inout, int64_t *count, int32_t set);
 /* Installs the network's M as the context's zero-lag solver (sweeps
- * x <- x + M (b - A x), count from ||I - M A||_inf so that the error stays
- * below solver_tol) when that takes fewer launches than Jacobi; otherwise
- * Jacobi stays.  *use_sai, *sweeps, *contraction report the choice. */
+ * x <- x + M (b - A x), one launch each, count from ||I - M A||_inf so that
+ * the error stays below solver_tol) when that takes fewer sweeps than
+ * Jacobi; otherwise Jacobi stays.  *use_sai, *sweeps, *contraction report the choice. */
 int tdbem_set_precond(tdbem_ctx *ctx, const tdbem_sai *sai, int32_t *use_sai, int32_t *sweeps, double *contraction);
+
+/* Checkpoint and resume at any step boundary (an addition of the library).
+ * The state is the u and q histories of the steps taken and, for the FMM,
+ * every level's moment accumulator, locals L_k..L_{k+mu+1}, derivative and
+ * auxiliary locals of Formula 1 and the current leaf far field.
+ * tdbem_checkpoint: buf = NULL sets *len to the size needed; otherwise buf
+ * (host, *len bytes) receives the state (synchronises).  tdbem_restore
+ * loads it into a context prepared for the same problem (same mesh, BC,
+ * known data, incident wave and parameters; ERR_ARG otherwise); stepping
+ * then continues exactly as the checkpointed context would. */
+int tdbem_checkpoint(const tdbem_ctx *ctx, void *buf, size_t *len);
+int tdbem_restore(tdbem_ctx *ctx, const void *buf, size_t len);
 
 /* Number of time steps taken so far (a_cur). */
 int tdbem_steps_done(const tdbem_ctx *ctx, int32_t *out);

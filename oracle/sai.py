@@ -5,39 +5,44 @@ Plain FP64 numpy restatement of the network and the training loss that the
 library uses for its zero-lag preconditioner (an addition of the library;
 the paper only says the system of Eq. linear is sparse):
 
-- row i's slots: the diagonal, then the off-diagonal nonzeros of A by
-  decreasing |A_ij| (ties by column), at most W;
-- features per slot: A_ij / A_ii, |x_i - x_j| / (c dt), 1 (zeros past the
-  row's length);
+- row i's slots: the diagonal, then the off-diagonal entries of A with
+  |A_ij| >= 1e-12 |A_ii| by decreasing |A_ij| (ties by column), at most W;
+- features per slot: A_ij/A_ii, A_jj/A_ii, A_ji/A_ii, |x_i - x_j|/(c dt), 1
+  (zeros past the row's length);
 - network: h = relu(W1 f + b1), o = W2 h + b2, M_ij = o_k / A_ii;
 - loss: sum_i || e_i^T - m_i^T A ||^2, and its gradient.
-Weight vector layout: W1 [H, 3W] row-major, b1 [H], W2 [W, H], b2 [W].
+Weight vector layout: W1 [H, 5W] row-major, b1 [H], W2 [W, H], b2 [W].
 """
 
 import numpy as np
 
 
+F = 5
+
+
 def row_slots(A, i, W):
-    cols = [int(j) for j in np.nonzero(A[i])[0] if j != i]
+    cols = [int(j) for j in np.nonzero(A[i])[0] if j != i and abs(A[i, j]) >= 1e-12 * abs(A[i, i])]
     cols.sort(key=lambda j: (-abs(A[i, j]), j))
     return [i] + cols[: W - 1]
 
 
 def features(A, xc, cdt, i, W):
     cols = row_slots(A, i, W)
-    f = np.zeros(3 * W)
+    f = np.zeros(F * W)
     for k, j in enumerate(cols):
-        f[3 * k] = A[i, j] / A[i, i]
-        f[3 * k + 1] = np.linalg.norm(xc[i] - xc[j]) / cdt
-        f[3 * k + 2] = 1.0
+        f[F * k] = A[i, j] / A[i, i]
+        f[F * k + 1] = A[j, j] / A[i, i]
+        f[F * k + 2] = A[j, i] / A[i, i]
+        f[F * k + 3] = np.linalg.norm(xc[i] - xc[j]) / cdt
+        f[F * k + 4] = 1.0
     return cols, f
 
 
 def unpack(w, W, H):
-    F = 3 * W
+    Fw = F * W
     o = 0
-    W1 = w[o:o + H * F].reshape(H, F)
-    o += H * F
+    W1 = w[o:o + H * Fw].reshape(H, Fw)
+    o += H * Fw
     b1 = w[o:o + H]
     o += H
     W2 = w[o:o + W * H].reshape(W, H)

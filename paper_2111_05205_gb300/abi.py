@@ -63,6 +63,8 @@ SIGNATURES = {
     "tdbem_step": (ctypes.c_int, [_P, _I]),
     "tdbem_step_io": (ctypes.c_int, [_P, _I, _P, _P, _I]),
     "tdbem_step_graph": (ctypes.c_int, [_P, _I]),
+    "tdbem_checkpoint": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tdbem_restore": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "tdbem_sai_create": (ctypes.c_int, [_I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
     "tdbem_sai_destroy": (None, [_P]),
     "tdbem_sai_last_error": (ctypes.c_char_p, [_P]),
@@ -268,6 +270,20 @@ def tdbem_set_precond(ctx, sai):
     use, sw, q = _I(), _I(), _D()
     _check(ctx, lib().tdbem_set_precond(ctx, sai, ctypes.byref(use), ctypes.byref(sw), ctypes.byref(q)))
     return bool(use.value), sw.value, q.value
+
+
+def tdbem_checkpoint(ctx):
+    """The context's state as bytes."""
+    n = ctypes.c_size_t()
+    _check(ctx, lib().tdbem_checkpoint(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, lib().tdbem_checkpoint(ctx, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def tdbem_restore(ctx, data):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(ctx, lib().tdbem_restore(ctx, buf, len(data)))
 
 
 def tdbem_steps_done(ctx):

@@ -475,7 +475,7 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
                     TD_CUDA(launch_jacobi(c, alpha, it, it == c->solve_iters - 1));
             }
         }
-        c->launches[PH_SOLVE] += c->sai_val ? 2 * c->sai_iters : c->solve_iters;
+        c->launches[PH_SOLVE] += c->sai_val ? c->sai_iters : c->solve_iters;
         c->alpha = alpha;
         c->steps_total += 1;
     }
@@ -794,6 +794,95 @@ int tdbem_get_tree(const tdbem_ctx *cc, int32_t what, int32_t level, void *out, 
     case TDBEM_TREE_IL: return csr(T.il, T.ilcount, 189, false);
     default: return fail(c, TDBEM_ERR_ARG, "unknown tree item");
     }
+}
+
+// Checkpoint layout: header (8 int64: magic, version, ns, nt, alpha, algo,
+// precision, far_k), u and q rows [0, alpha), then for the FMM, per level
+// 2..L: M, ring, D, A; then the current far field [Lt][ns].
+namespace {
+constexpr int64_t kCkptMagic = 0x544442454d434b50LL;  // "TDBEMCKP"
+
+struct CkptPart {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<CkptPart> ckpt_parts(tdbem_ctx *c)
+{
+    std::vector<CkptPart> v;
+    size_t rows = (size_t)c->alpha * c->ns * sizeof(double);
+    v.push_back({c->d_u, rows});
+    v.push_back({c->d_q, rows});
+    if (c->fmm.on) {
+        const size_t P = c->fmm.P;
+        for (int l = 2; l <= c->fmm.L; ++l) {
+            FmmLevel &V = c->fmm.lev[l];
+            v.push_back({V.M, (size_t)V.nc * P * sizeof(double)});
+            v.push_back({V.ring, (size_t)c->fmm.nslot * V.nc * P * sizeof(double)});
+            v.push_back({V.D, (size_t)std::max(c->P.d, 1) * V.nc * P * sizeof(double)});
+            v.push_back({V.A, (size_t)std::max(c->fmm.nd, 1) * V.nc * P * sizeof(double)});
+        }
+        v.push_back({c->fmm.far, (size_t)c->fmm.Lt * c->ns * sizeof(double)});
+    }
+    return v;
+}
+}  // namespace
+
+int tdbem_checkpoint(const tdbem_ctx *cc, void *buf, size_t *len)
+{
+    tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
+    if (!c || !len) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "checkpoint before prepare");
+    auto parts = ckpt_parts(c);
+    size_t need = 8 * sizeof(int64_t);
+    for (auto &p : parts) need += p.bytes;
+    if (!buf) {
+        *len = need;
+        return TDBEM_OK;
+    }
+    if (*len < need) return fail(c, TDBEM_ERR_ARG, "checkpoint buffer too small");
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    int64_t h[8] = {kCkptMagic, 1, c->ns, c->P.nt, c->alpha, c->P.algo, c->P.precision, c->fmm.far_k};
+    char *o = (char *)buf;
+    memcpy(o, h, sizeof(h));
+    o += sizeof(h);
+    for (auto &p : parts) {
+        if (p.bytes) TD_CUDA(cudaMemcpy(o, p.dev, p.bytes, cudaMemcpyDeviceToHost));
+        o += p.bytes;
+    }
+    *len = need;
+    return TDBEM_OK;
+}
+
+int tdbem_restore(tdbem_ctx *c, const void *buf, size_t len)
+{
+    if (!c || !buf) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "restore before prepare");
+    int64_t h[8];
+    if (len < sizeof(h)) return fail(c, TDBEM_ERR_ARG, "checkpoint too short");
+    memcpy(h, buf, sizeof(h));
+    if (h[0] != kCkptMagic || h[1] != 1 || h[2] != c->ns || h[3] != c->P.nt || h[5] != c->P.algo ||
+        h[6] != c->P.precision || h[4] < 0 || h[4] > c->P.nt - 1)
+        return fail(c, TDBEM_ERR_ARG, "checkpoint of another problem or format");
+    int keep = c->alpha;
+    c->alpha = (int)h[4];
+    auto parts = ckpt_parts(c);
+    size_t need = sizeof(h);
+    for (auto &p : parts) need += p.bytes;
+    if (len < need) {
+        c->alpha = keep;
+        return fail(c, TDBEM_ERR_ARG, "checkpoint truncated");
+    }
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    const char *o = (const char *)buf + sizeof(h);
+    for (auto &p : parts) {
+        if (p.bytes) TD_CUDA(cudaMemcpy(p.dev, o, p.bytes, cudaMemcpyHostToDevice));
+        o += p.bytes;
+    }
+    c->fmm.far_k = (int)h[7];
+    if (c->split) TD_CUDA(launch_split_histories(c));
+    TD_CUDA(cudaStreamSynchronize(c->s));
+    return TDBEM_OK;
 }
 
 int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)

@@ -28,6 +28,7 @@
 namespace tdbem {
 
 constexpr int kMaxP = 8;
+constexpr int kBuckets = 8;  // groups of offsets (by pair count) of the batched M2L GEMMs
 
 __device__ __forceinline__ double cheb_node(int p, int a) { return cos((2.0 * a + 1.0) * 3.14159265358979323846 / (2.0 * p)); }
 
@@ -125,18 +126,19 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
     }
 }
 
-// M2L operator bank of one level: op[o][blk][row][col] with o = (dx+3) +
-// 7((dy+3) + 7(dz+3)) the cell offset S - O, blk = l-1 (near future l =
+// M2L operator bank of one level: op[t][blk][row][col] for the offsets
+// o = offs[t] = (dx+3) + 7((dy+3) + 7(dz+3)) (the cell offset S - O) in the
+// order the batched GEMMs use, blk = l-1 (near future l =
 // 1..mu+1) or mu+p (the p-th derivative U^(p) at I_{k+mu+1}, Eq. U_expand),
 // row = a + P3 m, col = b + P3 n:
 //   U(x_a, y_b, t_m, s_n) = (c (t_m - s_n) - r)_+^d / r,
 //   U^(p) = C(d, p) (c (t_m - s_n) - r)_+^(d-p) / r,
 // x_a - y_b = -offset s + h (w_a - w_b), t_m - s_n = l T dt + dt + ht (w_m - w_n).
 __global__ void k_m2l_operators(int ps, int pt, int d, int mu, double s, double hs, double T_dt, double dt,
-                                double ht, double c, double *op)
+                                double ht, double c, int noff, const int32_t *__restrict__ offs, double *op)
 {
     const int P3 = ps * ps * ps, P = P3 * pt, nblk = mu + 1 + d;
-    int64_t total = 343LL * nblk * P * P;
+    int64_t total = (int64_t)noff * nblk * P * P;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int col = (int)(e % P);
@@ -144,7 +146,7 @@ __global__ void k_m2l_operators(int ps, int pt, int d, int mu, double s, double 
         int row = (int)(r1 % P);
         int64_t r2 = r1 / P;
         int blk = (int)(r2 % nblk);
-        int o = (int)(r2 / nblk);
+        int o = offs[r2 / nblk];
         int dx = o % 7 - 3, dy = (o / 7) % 7 - 3, dz = o / 49 - 3;
         if (max(abs(dx), max(abs(dy), abs(dz))) <= 1) {
             op[e] = 0.0;
@@ -658,8 +660,6 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             F_TRY(falloc(c, &V.Sm, sm.size()));
             F_TRY(cudaMemcpyAsync(V.Sm, sm.data(), sm.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
         }
-        size_t nop = (size_t)343 * F.nblk * P * P;
-        F_TRY(falloc(c, &V.op, nop));
         // interaction pairs grouped by offset, and per observation cell
         {
             const TreeLevel &T = c->tree.levels[l];
@@ -692,13 +692,36 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             }
             V.ostart[343] = (int64_t)pS.size();
             V.np = (int64_t)pS.size();
-            // every offset's pairs occupy a slab of nmax columns (zero-padded)
-            // so that one strided-batched GEMM covers all offsets
-            V.nmax = 0;
-            for (int o = 0; o < 343; ++o) V.nmax = std::max<int64_t>(V.nmax, V.ostart[o + 1] - V.ostart[o]);
-            std::vector<int64_t> pcol(V.np);
+            // offsets sorted by pair count are cut into kBuckets groups; each
+            // offset of a group owns a slab of the group's largest pair count
+            // (zero-padded), so one batched GEMM per group covers it
+            std::vector<int> ord;
             for (int o = 0; o < 343; ++o)
-                for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = (int64_t)o * V.nmax + (t - V.ostart[o]);
+                if (V.ostart[o + 1] > V.ostart[o]) ord.push_back(o);
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+                return V.ostart[a + 1] - V.ostart[a] > V.ostart[b + 1] - V.ostart[b];
+            });
+            std::vector<int64_t> colbase(343, 0), pcol(V.np);
+            V.buckets.clear();
+            int64_t col = 0;
+            const int nbk = std::min<int>(kBuckets, (int)ord.size());
+            for (int bk = 0; bk < nbk; ++bk) {
+                size_t lo = ord.size() * bk / nbk, hi = ord.size() * (bk + 1) / nbk;
+                FmmBucket B;
+                B.first = (int)lo;
+                B.count = (int)(hi - lo);
+                B.n = V.ostart[ord[lo] + 1] - V.ostart[ord[lo]];
+                for (size_t t = lo; t < hi; ++t) {
+                    colbase[ord[t]] = col;
+                    col += B.n;
+                }
+                V.buckets.push_back(B);
+            }
+            V.ncol = std::max<int64_t>(col, 1);
+            for (int o = 0; o < 343; ++o)
+                for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = colbase[o] + (t - V.ostart[o]);
+            V.ord = ord;
+            V.colbase = colbase;
             std::vector<int64_t> ooff(V.nc + 1, 0);
             for (int32_t O : pO) ooff[O + 1]++;
             for (int O = 0; O < V.nc; ++O) ooff[O + 1] += ooff[O];
@@ -712,7 +735,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             F_TRY(cudaMemcpyAsync(V.pcol, pcol.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
             F_TRY(cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
             F_TRY(cudaMemcpyAsync(V.oidx, oidx.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
-            size_t ncol = (size_t)343 * V.nmax;
+            size_t ncol = (size_t)V.ncol;
             if (c->split) {
                 F_TRY(falloc(c, &V.Bbuf32, ncol * P));
                 F_TRY(falloc(c, &V.Cbuf32, ncol * F.nblk * P));
@@ -723,19 +746,30 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             F_TRY(cudaStreamSynchronize(c->s));
         }
         double Tdt = V.T * c->P.dt;
-        k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, V.s, V.hs, Tdt, c->P.dt, Tdt / 2.0, c->P.c,
-                                                    V.op);
-        F_TRY(cudaGetLastError());
-        if (c->split) {
-            // mixed form: FP32 operators for the emulated-FP32 tensor-core GEMM
-            F_TRY(falloc(c, &V.op32, nop));
-            k_to_float<<<152 * 32, 256, 0, c->s>>>((int64_t)nop, V.op, V.op32);
+        {
+            // operators of the offsets that occur, in bucket order
+            size_t noff = std::max<size_t>(V.ord.size(), 1);
+            size_t nop = noff * F.nblk * P * P;
+            F_TRY(falloc(c, &V.op, nop));
+            int32_t *d_offs = nullptr;
+            F_TRY(falloc(c, &d_offs, noff));
+            if (!V.ord.empty())
+                F_TRY(cudaMemcpyAsync(d_offs, V.ord.data(), V.ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                      c->s));
+            k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, V.s, V.hs, Tdt, c->P.dt, Tdt / 2.0, c->P.c,
+                                                        (int)V.ord.size(), d_offs, V.op);
             F_TRY(cudaGetLastError());
-            F_TRY(cudaStreamSynchronize(c->s));
-            auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)V.op);
-            if (it != c->allocs.end()) c->allocs.erase(it);
-            cudaFree(V.op);
-            V.op = nullptr;
+            if (c->split) {
+                // mixed form: FP32 operators for the emulated-FP32 tensor-core GEMM
+                F_TRY(falloc(c, &V.op32, nop));
+                k_to_float<<<152 * 32, 256, 0, c->s>>>((int64_t)nop, V.op, V.op32);
+                F_TRY(cudaGetLastError());
+                F_TRY(cudaStreamSynchronize(c->s));
+                auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)V.op);
+                if (it != c->allocs.end()) c->allocs.erase(it);
+                cudaFree(V.op);
+                V.op = nullptr;
+            }
         }
         V.Tlen = c->P.c * Tdt;
     }
@@ -768,28 +802,42 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
             const int R = F.nblk * P;
             cudaEvent_t ev;
             phase_begin(c, &ev);
-            const long long sA = (long long)R * P, sB = (long long)V.nmax * P, sC = (long long)V.nmax * R;
-            cublasStatus_t st;
+            cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+            const long long sA = (long long)R * P;
             if (c->split) {
                 // FP32 operands, FP32-accurate products on the BF16 tensor
                 // cores (three BF16 terms per operand), FP64 locals
                 k_m2l_gather<float><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf32);
                 const float one = 1.0f, zero = 0.0f;
-                st = cublasGemmStridedBatchedEx(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)V.nmax, P, &one, V.op32,
-                                                CUDA_R_32F, P, sA, V.Bbuf32, CUDA_R_32F, P, sB, &zero, V.Cbuf32,
-                                                CUDA_R_32F, R, sC, 343, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                                                CUBLAS_GEMM_DEFAULT);
+                for (const FmmBucket &B : V.buckets) {
+                    if (st != CUBLAS_STATUS_SUCCESS) break;
+                    int64_t cb = V.colbase[V.ord[B.first]];
+                    st = cublasGemmStridedBatchedEx(
+                        F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one, V.op32 + (size_t)B.first * sA,
+                        CUDA_R_32F, P, sA, V.Bbuf32 + (size_t)cb * P, CUDA_R_32F, P, (long long)B.n * P, &zero,
+                        V.Cbuf32 + (size_t)cb * R, CUDA_R_32F, R, (long long)B.n * R, B.count,
+                        CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+                }
                 k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf32,
                                                          V.ring, V.G);
             } else {
                 k_m2l_gather<double><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf);
                 const double one = 1.0, zero = 0.0;
-                st = cublasDgemmStridedBatched(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)V.nmax, P, &one, V.op, P, sA,
-                                               V.Bbuf, P, sB, &zero, V.Cbuf, R, sC, 343);
+                for (const FmmBucket &B : V.buckets) {
+                    if (st != CUBLAS_STATUS_SUCCESS) break;
+                    int64_t cb = V.colbase[V.ord[B.first]];
+                    st = cublasDgemmStridedBatched(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one,
+                                                   V.op + (size_t)B.first * sA, P, sA, V.Bbuf + (size_t)cb * P, P,
+                                                   (long long)B.n * P, &zero, V.Cbuf + (size_t)cb * R, R,
+                                                   (long long)B.n * R, B.count);
+                }
                 k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf,
                                                           V.ring, V.G);
             }
-            if (st != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+            if (st != CUBLAS_STATUS_SUCCESS) {
+                c->err = "cuBLAS status " + std::to_string((int)st) + " in the M2L GEMM";
+                return cudaErrorUnknown;
+            }
             phase_end(c, PH_M2L, ev);
             c->launches[PH_M2L] += 1;
             c->m2l_flops += 2.0 * (double)R * P * (double)V.np;  // algorithmic (unpadded) flops

@@ -7,8 +7,10 @@
 // row of a left SAI M on the same pattern; the zero-lag solve then runs
 // preconditioned Richardson sweeps x <- x + M (b - A x) instead of Jacobi
 // sweeps (Jacobi is M = D^-1).  Features of slot k (k = 0: the diagonal;
-// then the off-diagonal entries by decreasing |A_ij|): A_ij / A_ii, the
-// distance |x_i - x_j| / (c dt) and a validity flag.  Network: in = 3W ->
+// then the off-diagonal entries by decreasing |A_ij|): A_ij/A_ii, A_jj/A_ii,
+// A_ji/A_ii (what the first Neumann term -A_ij/(A_ii A_jj) of A^-1 and the
+// symmetry of the pattern depend on), the distance |x_i - x_j| / (c dt) and
+// a validity flag.  Network: in = 5W ->
 // hidden H (ReLU) -> W outputs o_k, M_ij = o_k / A_ii.  FP16 weights, FP32
 // arithmetic.  Training minimises sum_i || e_i^T - m_i^T A ||^2 over rows
 // of zero-lag matrices the method assembles, with hand-written forward,
@@ -24,15 +26,29 @@ namespace tdbem {
 constexpr int kSaiMaxW = 16;
 constexpr int kSaiMaxH = 64;
 
+constexpr int kSaiF = 5;  // features per slot
+
 struct SaiRow {
     int n;                 // valid slots (diagonal first)
     int col[kSaiMaxW];
-    float feat[3 * kSaiMaxW];
+    float feat[kSaiF * kSaiMaxW];
     double inv_diag;
 };
 
+// Entry A_jl (l any column) from the ELL store.
+__device__ __forceinline__ double a_entry(int j, int l, int ns, int ell_w, const double *aoff, const int32_t *acol,
+                                          const double *ainv)
+{
+    if (j == l) return 1.0 / ainv[j];
+    for (int k = 0; k < ell_w; ++k)
+        if (acol[(int64_t)k * ns + j] == l) return aoff[(int64_t)k * ns + j];
+    return 0.0;
+}
+
 // Slots of row i in the canonical order: the diagonal, then off-diagonal
-// entries by decreasing magnitude (ties by column).
+// entries with |A_ij| >= 1e-12 |A_ii| by decreasing magnitude (ties by
+// column).  Features of slot k (column j): A_ij/A_ii, A_jj/A_ii, A_ji/A_ii,
+// |x_i - x_j|/(c dt), 1.
 __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, const int32_t *acol,
                         const double *ainv, const double *xc, double cdt, SaiRow &R)
 {
@@ -46,6 +62,7 @@ __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, con
         int j = acol[(int64_t)k * ns + i];
         if (j < 0) continue;
         double v = aoff[(int64_t)k * ns + i];
+        if (!(fabs(v) >= 1e-12 * fabs(ad))) continue;
         int p = n++;
         while (p > 1 && (fabs(vals[p - 1]) < fabs(v) || (fabs(vals[p - 1]) == fabs(v) && cols[p - 1] > j))) {
             vals[p] = vals[p - 1];
@@ -66,9 +83,12 @@ __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, con
             dy = xc[3 * i + 1] - xc[3 * cols[k] + 1];
             dz = xc[3 * i + 2] - xc[3 * cols[k] + 2];
         }
-        R.feat[3 * k] = ok ? (float)(vals[k] * ainv[i]) : 0.f;
-        R.feat[3 * k + 1] = ok ? (float)(sqrt(dx * dx + dy * dy + dz * dz) / cdt) : 0.f;
-        R.feat[3 * k + 2] = ok ? 1.f : 0.f;
+        float *f = R.feat + kSaiF * k;
+        f[0] = ok ? (float)(vals[k] * ainv[i]) : 0.f;
+        f[1] = ok ? (float)(ainv[i] / ainv[cols[k]]) : 0.f;
+        f[2] = ok ? (float)(a_entry(cols[k], i, ns, ell_w, aoff, acol, ainv) * ainv[i]) : 0.f;
+        f[3] = ok ? (float)(sqrt(dx * dx + dy * dy + dz * dz) / cdt) : 0.f;
+        f[4] = ok ? 1.f : 0.f;
     }
 }
 
@@ -76,7 +96,7 @@ __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, con
 __device__ void sai_forward(int W, int H, const __half *w1, const __half *b1, const __half *w2, const __half *b2,
                             const float *in, float *h, float *o)
 {
-    const int F = 3 * W;
+    const int F = kSaiF * W;
     for (int a = 0; a < H; ++a) {
         float s = __half2float(b1[a]);
         for (int f = 0; f < F; ++f) s += __half2float(w1[a * F + f]) * in[f];
@@ -87,16 +107,6 @@ __device__ void sai_forward(int W, int H, const __half *w1, const __half *b1, co
         for (int a = 0; a < H; ++a) s += __half2float(w2[k * H + a]) * h[a];
         o[k] = s;
     }
-}
-
-// Entry A_jl (l any column) from the ELL store.
-__device__ __forceinline__ double a_entry(int j, int l, int ns, int ell_w, const double *aoff, const int32_t *acol,
-                                          const double *ainv)
-{
-    if (j == l) return 1.0 / ainv[j];
-    for (int k = 0; k < ell_w; ++k)
-        if (acol[(int64_t)k * ns + j] == l) return aoff[(int64_t)k * ns + j];
-    return 0.0;
 }
 
 // One training pass over the rows of one matrix: loss of every row and the
@@ -110,7 +120,7 @@ __global__ void k_sai_train_rows(int ns, int ell_w, int W, int H, const double *
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
-    const int F = 3 * W;
+    const int F = kSaiF * W;
     const __half *w1 = w16, *b1 = w1 + H * F, *w2 = b1 + H, *b2 = w2 + W * H;
     float *g1 = grad, *gb1 = g1 + H * F, *g2 = gb1 + H, *gb2 = g2 + W * H;
     SaiRow R;
@@ -191,7 +201,7 @@ __global__ void k_sai_apply_net(int ns, int ell_w, int W, int H, const double *_
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
-    const int F = 3 * W;
+    const int F = kSaiF * W;
     const __half *w1 = w16, *b1 = w1 + H * F, *w2 = b1 + H, *b2 = w2 + W * H;
     SaiRow R;
     sai_row(i, ns, ell_w, W, aoff, acol, ainv, xc, cdt, R);
@@ -203,37 +213,31 @@ __global__ void k_sai_apply_net(int ns, int ell_w, int W, int H, const double *_
     }
 }
 
-// Residual r = b - A x (x == nullptr: r = b).
-__global__ void k_residual(int ns, int ell_w, const double *__restrict__ aoff, const int32_t *__restrict__ acol,
-                           const double *__restrict__ ainv, const double *__restrict__ b,
-                           const double *__restrict__ x, double *r)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
-    double s = b[i];
-    if (x) {
-        s -= x[i] / ainv[i];
-        for (int k = 0; k < ell_w; ++k) {
-            int j = acol[(int64_t)k * ns + i];
-            if (j >= 0) s -= aoff[(int64_t)k * ns + i] * x[j];
-        }
-    }
-    r[i] = s;
-}
-
-// x' = x + M r (x == nullptr: x' = M r); the last sweep adds x' to the
-// unknown component of step a-1 (as the Jacobi sweep does).
-__global__ void k_sai_update(int ns, int W, const double *__restrict__ mval, const int32_t *__restrict__ mcol,
-                             const double *__restrict__ r, const double *__restrict__ x, double *xout, int last,
-                             int64_t row, const int8_t *__restrict__ phi, double *u, double *q, float2 *us,
-                             float2 *qs, int *flag)
+// One preconditioned sweep x' = x + M (b - A x) (x == nullptr: x' = M b),
+// the residual of each row j of M's pattern recomputed on the fly (one
+// launch per sweep, as the Jacobi sweep).  The last sweep adds x' to the
+// unknown component of step a-1.
+__global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__ mval, const int32_t *__restrict__ mcol,
+                            const double *__restrict__ aoff, const int32_t *__restrict__ acol,
+                            const double *__restrict__ ainv, const double *__restrict__ b,
+                            const double *__restrict__ x, double *xout, int last, int64_t row,
+                            const int8_t *__restrict__ phi, double *u, double *q, float2 *us, float2 *qs, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     double s = x ? x[i] : 0.0;
     for (int k = 0; k < W; ++k) {
         int j = mcol[(int64_t)k * ns + i];
-        if (j >= 0) s += mval[(int64_t)k * ns + i] * r[j];
+        if (j < 0) continue;
+        double r = b[j];
+        if (x) {
+            r -= x[j] / ainv[j];
+            for (int e = 0; e < ell_w; ++e) {
+                int l = acol[(int64_t)e * ns + j];
+                if (l >= 0) r -= aoff[(int64_t)e * ns + j] * x[l];
+            }
+        }
+        s += mval[(int64_t)k * ns + i] * r;
     }
     if (last) {
         double *hh = phi[i] ? u : q;
@@ -287,7 +291,7 @@ int tdbem_sai_create(int32_t width, int32_t hidden, uint64_t seed, tdbem_sai **o
     tdbem_sai *S = new tdbem_sai();
     S->W = width;
     S->H = hidden;
-    const int F = 3 * width;
+    const int F = kSaiF * width;
     S->nw = hidden * F + hidden + width * hidden + width;
     std::vector<float> w(S->nw, 0.f);
     uint64_t st = seed;
@@ -464,8 +468,8 @@ int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_
     }
     double tol = c->P.solver_tol > 0 ? c->P.solver_tol : 1e-16;
     int K = (qmax > 0.0 && qmax < 1.0) ? std::max(1, (int)ceil(log(tol) / log(qmax))) : 1 << 30;
-    // a preconditioned sweep is two launches (residual, update); the first is one
-    bool better = qmax < 1.0 && (2 * K - 1) < c->solve_iters;
+    // one launch per sweep for either solver
+    bool better = qmax < 1.0 && K < c->solve_iters;
     if (better) {
         c->sai_val = mval;
         c->sai_col = mcol;
@@ -490,11 +494,10 @@ cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it)
     const bool last = (it == c->sai_iters - 1);
     const double *xin = (it == 0) ? nullptr : ((it & 1) ? c->d_xa : c->d_xb);
     double *xout = (it & 1) ? c->d_xb : c->d_xa;
-    double *r = c->d_r;
-    k_residual<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->ell_w, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, r);
     int64_t row = (int64_t)(alpha - 1) * ns;
-    k_sai_update<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->sai_w, c->sai_val, c->sai_col, r, xin, xout, last, row,
-                                                     c->d_phi, c->d_u, c->d_q, c->d_us, c->d_qs, c->d_flag);
+    k_sai_sweep<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->sai_w, c->ell_w, c->sai_val, c->sai_col, c->d_aoff,
+                                                    c->d_acol, c->d_ainv, c->d_b, xin, xout, last, row, c->d_phi,
+                                                    c->d_u, c->d_q, c->d_us, c->d_qs, c->d_flag);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,12 @@ struct Tree {
     std::vector<TreeLevel> levels;
 };
 
+// A group of cell offsets whose M2L GEMMs run as one batched call.
+struct FmmBucket {
+    int first = 0, count = 0;    // range in the level's offset order
+    int64_t n = 0;               // columns per offset (the group's largest pair count)
+};
+
 // One level of the space-time FMM (device arrays; levels 2..L).
 struct FmmLevel {
     int nc = 0;
@@ -58,13 +64,16 @@ struct FmmLevel {
     double *D = nullptr;         // [d][nc][P] derivative locals L^(p)
     double *A = nullptr;         // [n_d][nc][P] auxiliary locals L^(p,m)
     double *G = nullptr;         // [d][nc][P] contributions L^(p)_{k+mu+1,k}
-    double *op = nullptr;        // [343][mu+1+d][P][P] M2L operators
+    double *op = nullptr;        // [offsets in bucket order][mu+1+d][P][P] M2L operators
     double *Sm = nullptr;        // [2][ps][ps] transfer to the parent level
     // interaction pairs grouped by offset for the GEMM form of the M2L
     int64_t np = 0;              // pairs
     std::vector<int64_t> ostart; // [344] first pair of each offset
     int32_t *pS = nullptr;       // [np] source cell of each pair
-    int64_t nmax = 0;            // columns per offset slab (the busiest offset's pairs)
+    int64_t ncol = 0;            // columns of the gathered-moment buffer
+    std::vector<int> ord;        // offsets with pairs, by decreasing pair count
+    std::vector<int64_t> colbase;  // [343] first column of each offset's slab
+    std::vector<FmmBucket> buckets;
     int64_t *pcol = nullptr;     // [np] padded column of each pair
     int64_t *ooff = nullptr;     // [nc+1] pairs of each observation cell (CSR)
     int64_t *oidx = nullptr;     // [np] their padded columns

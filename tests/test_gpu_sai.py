@@ -6,8 +6,9 @@
    1e-3 relative (FP32 accumulation over the rows).
 2. After training on the GPU on zero-lag matrices assembled by the library
    from seeded random ellipsoids, the learned M solves the zero-lag system
-   of a held-out mesh with fewer kernel launches than Jacobi, and the
-   marching solution equals the Jacobi one (1e-12: both solve to 1e-16).
+   of a held-out mesh in fewer sweeps (one launch each) than Jacobi, by the
+   a-priori bound of ||I - M A||_inf, and the marching solution equals the
+   Jacobi one (1e-12: both solve to 1e-16).
 """
 
 import numpy as np
@@ -58,14 +59,14 @@ def test_learned_sai_beats_jacobi_on_a_held_out_mesh():
     sai = abi.tdbem_sai_create(12, 32, 3)
     try:
         L0 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 1, 0.0)
-        L1 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 60, 3e-3)
+        L1 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 150, 2e-3)
         assert L1 < 0.5 * L0, (L0, L1)
         w = workload("ellipsoid1280_bmbie_d2_hard_plane_s99", nt=30)
         a, b = gpu_solver(w), gpu_solver(w)
         try:
             kj = a.stats()["solve_iters"]
             use, sweeps, q = abi.tdbem_set_precond(b.ctx, sai)
-            assert use and 2 * sweeps - 1 < kj, (use, sweeps, q, kj)
+            assert use and sweeps < kj, (use, sweeps, q, kj)
             abi.tdbem_step(a.ctx, 29)
             abi.tdbem_step(b.ctx, 29)
             ua, _ = a.solution()
