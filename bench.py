@@ -331,7 +331,8 @@ def run_ours(args):
                                "meets_1e-3": bool(max(err) <= 1e-3), "m2l_tflops": m2l_tf,
                                "m2l_ms_per_step": stf["ms_m2l"] / args.steps,
                                "near_ms_per_step": stf["ms_near"] / args.steps,
-                               "far_ms_per_step": stf["ms_far"] / args.steps, "setup_s": round(fsetup, 2)}
+                               "far_ms_per_step": stf["ms_far"] / args.steps, "setup_s": round(fsetup, 2),
+                               "m2l_buckets_by_level": stf["m2l_buckets"][:args.depth + 1]}
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, rows=args.cpu_rows)

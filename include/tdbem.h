@@ -108,6 +108,8 @@ typedef struct {
     double ms_m2l;                 /* FMM: gather + M2L GEMMs + reduction, all levels */
     int64_t launches_m2l;          /* FMM: level M2L applications */
     double m2l_flops;              /* FMM: 2 (mu+1+d) P^2 per interaction pair and application */
+    int32_t m2l_buckets[11];       /* FMM: batched-GEMM groups per level chosen by the setup-time
+                                      autotuner (0 for levels without interaction pairs) */
 } tdbem_stats;
 
 /* Creates a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -194,12 +196,13 @@ const char *tdbem_batch_last_error(const tdbem_batch *batch);
  * outputs, FP16 weights, FP32 arithmetic) that maps the features of row i
  * of A (per slot k, the diagonal first and then the off-diagonal entries
  * with |A_ij| >= 1e-12 |A_ii| by decreasing |A_ij|: A_ij/A_ii, A_jj/A_ii,
- * A_ji/A_ii, |x_i - x_j|/(c dt), 1) to the row of a left SAI M on that
- * pattern (M_ij = output_k / A_ii).  Training minimises
+ * A_ji/A_ii, |x_i - x_j|/(c dt), 1) to a correction of the row of a left
+ * SAI M on that pattern: M_ij = (base_k + output_k) / A_ii with base 1 on the
+ * diagonal and the first Neumann term -A_ij/A_jj off it.  Training minimises
  * sum_i ||e_i^T - m_i^T A||^2 over the rows of prepared contexts (their
  * zero-lag matrices; a context with nt = 2 computes only those) with Adam,
  * one update per context and pass, all on the GPU.  width 2..16, hidden
- * 1..64; the weights start from Jacobi (M = D^-1). */
+ * 1..64; the output layer starts near zero (M = the Neumann SAI). */
 typedef struct tdbem_sai tdbem_sai;
 int tdbem_sai_create(int32_t width, int32_t hidden, uint64_t seed, tdbem_sai **out);
 void tdbem_sai_destroy(tdbem_sai *sai);

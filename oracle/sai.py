@@ -6,10 +6,13 @@ library uses for its zero-lag preconditioner (an addition of the library;
 the paper only says the system of Eq. linear is sparse):
 
 - row i's slots: the diagonal, then the off-diagonal entries of A with
-  |A_ij| >= 1e-12 |A_ii| by decreasing |A_ij| (ties by column), at most W;
+  |A_ij| >= 1e-12 |A_ii| by decreasing |A_ij|/|A_ii| quantised to 2^-20
+  (ties by column), at most W;
 - features per slot: A_ij/A_ii, A_jj/A_ii, A_ji/A_ii, |x_i - x_j|/(c dt), 1
   (zeros past the row's length);
-- network: h = relu(W1 f + b1), o = W2 h + b2, M_ij = o_k / A_ii;
+- network: h = relu(W1 f + b1), o = W2 h + b2 + base, M_ij = o_k / A_ii,
+  with the analytic part base_0 = 1 (Jacobi) and base_k = -A_ij / A_jj for
+  the off-diagonal slots (first Neumann term of A^-1, in units of 1/A_ii);
 - loss: sum_i || e_i^T - m_i^T A ||^2, and its gradient.
 Weight vector layout: W1 [H, 5W] row-major, b1 [H], W2 [W, H], b2 [W].
 """
@@ -22,7 +25,9 @@ F = 5
 
 def row_slots(A, i, W):
     cols = [int(j) for j in np.nonzero(A[i])[0] if j != i and abs(A[i, j]) >= 1e-12 * abs(A[i, i])]
-    cols.sort(key=lambda j: (-abs(A[i, j]), j))
+    # magnitude quantised to 2^-20 of |A_ii| (entries equal up to rounding
+    # keep one order), then column
+    cols.sort(key=lambda j: (-int(np.floor(abs(A[i, j] * (1.0 / A[i, i])) * 1048576.0)), j))
     return [i] + cols[: W - 1]
 
 
@@ -62,7 +67,10 @@ def loss_and_grad(w, A, xc, cdt, W, H):
         cols, f = features(A, xc, cdt, i, W)
         z = W1 @ f + b1
         h = np.maximum(z, 0.0)
-        o = W2 @ h + b2
+        base = np.zeros(W)
+        for k in range(len(cols)):
+            base[k] = 1.0 if k == 0 else -f[F * k] / f[F * k + 1]
+        o = W2 @ h + b2 + base
         n = len(cols)
         m = np.zeros(ns)
         for k in range(n):

@@ -899,6 +899,7 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->ms_m2l = c->ms[PH_M2L];
     o->launches_m2l = c->launches[PH_M2L];
     o->m2l_flops = c->m2l_flops;
+    for (int l = 0; l < 11 && l < (int)c->fmm.lev.size(); ++l) o->m2l_buckets[l] = c->fmm.lev[l].np ? c->fmm.lev[l].nbk : 0;
     o->launches_far = c->launches[PH_FAR];
     o->fmm_lt = c->fmm.Lt;
     o->fmm_mu = c->fmm.mu;

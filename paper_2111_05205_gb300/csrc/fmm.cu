@@ -28,7 +28,6 @@
 namespace tdbem {
 
 constexpr int kMaxP = 8;
-constexpr int kBuckets = 8;  // groups of offsets (by pair count) of the batched M2L GEMMs
 
 __device__ __forceinline__ double cheb_node(int p, int a) { return cos((2.0 * a + 1.0) * 3.14159265358979323846 / (2.0 * p)); }
 
@@ -524,6 +523,115 @@ void cmp_table(int d, int k, double *out)
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
+// Groups the level's offsets (in pair-count order) into nbk buckets of equal
+// offset count; each offset owns a slab of its bucket's largest pair count.
+static void m2l_layout(FmmLevel &V, int nbk)
+{
+    nbk = std::max(1, std::min<int>(nbk, (int)V.ord.size()));
+    V.colbase.assign(343, 0);
+    V.buckets.clear();
+    int64_t col = 0;
+    for (int bk = 0; bk < nbk; ++bk) {
+        size_t lo = V.ord.size() * bk / nbk, hi = V.ord.size() * (bk + 1) / nbk;
+        if (hi <= lo) continue;
+        FmmBucket B;
+        B.first = (int)lo;
+        B.count = (int)(hi - lo);
+        B.n = V.ostart[V.ord[lo] + 1] - V.ostart[V.ord[lo]];
+        for (size_t t = lo; t < hi; ++t) {
+            V.colbase[V.ord[t]] = col;
+            col += B.n;
+        }
+        V.buckets.push_back(B);
+    }
+    V.ncol = std::max<int64_t>(col, 1);
+    V.nbk = nbk;
+}
+
+// The batched GEMMs of one M2L application (operator stacks x gathered moments).
+static cublasStatus_t m2l_gemms(tdbem_ctx *c, FmmLevel &V)
+{
+    Fmm &F = c->fmm;
+    const int P = F.P, R = F.nblk * P;
+    const long long sA = (long long)R * P;
+    cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+    for (const FmmBucket &B : V.buckets) {
+        if (st != CUBLAS_STATUS_SUCCESS) break;
+        int64_t cb = V.colbase[V.ord[B.first]];
+        if (c->split) {
+            const float one = 1.0f, zero = 0.0f;
+            st = cublasGemmStridedBatchedEx(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one,
+                                            V.op32 + (size_t)B.first * sA, CUDA_R_32F, P, sA,
+                                            V.Bbuf32 + (size_t)cb * P, CUDA_R_32F, P, (long long)B.n * P, &zero,
+                                            V.Cbuf32 + (size_t)cb * R, CUDA_R_32F, R, (long long)B.n * R, B.count,
+                                            CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+        } else {
+            const double one = 1.0, zero = 0.0;
+            st = cublasDgemmStridedBatched(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one,
+                                           V.op + (size_t)B.first * sA, P, sA, V.Bbuf + (size_t)cb * P, P,
+                                           (long long)B.n * P, &zero, V.Cbuf + (size_t)cb * R, R, (long long)B.n * R,
+                                           B.count);
+        }
+    }
+    return st;
+}
+
+// Autotuner: times the level's M2L GEMMs for 1, 2, 4, .. 32 buckets on the
+// real operators and shapes, keeps the fastest, and uploads the pair
+// columns of that layout.
+static cudaError_t m2l_tune_and_finalize(tdbem_ctx *c, FmmLevel &V)
+{
+    cudaStream_t s = c->s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 1;
+    float best_ms = 1e30f;
+    V.tune.clear();
+    for (int nbk = 1; nbk <= 32; nbk *= 2) {
+        if (nbk > 1 && nbk > (int)V.ord.size()) break;
+        m2l_layout(V, nbk);
+        if (m2l_gemms(c, V) != CUBLAS_STATUS_SUCCESS) continue;  // warm-up; skip layouts the library rejects
+        cudaEventRecord(e0, s);
+        cublasStatus_t st = m2l_gemms(c, V);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st != CUBLAS_STATUS_SUCCESS) continue;
+        V.tune.push_back({nbk, ms});
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = nbk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30f) return cudaErrorUnknown;
+    m2l_layout(V, best);
+    std::vector<int64_t> pcol(V.np);
+    for (int o = 0; o < 343; ++o)
+        for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = V.colbase[o] + (t - V.ostart[o]);
+    std::vector<int64_t> ooff(V.nc + 1, 0);
+    for (int32_t O : V.hpO) ooff[O + 1]++;
+    for (int O = 0; O < V.nc; ++O) ooff[O + 1] += ooff[O];
+    std::vector<int64_t> oidx(V.np), fill(ooff.begin(), ooff.end() - 1);
+    for (int64_t t = 0; t < V.np; ++t) oidx[fill[V.hpO[t]]++] = pcol[t];
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(V.pS, V.hpS.data(), V.np * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(V.pcol, pcol.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(V.oidx, oidx.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    V.hpO.clear();
+    V.hpS.clear();
+    return cudaStreamSynchronize(s);
+}
+
 // Hierarchy parameters, per-element P2M/L2P tables, transfer matrices and
 // the M2L operator banks (setup; after the tree is built).
 cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
@@ -692,50 +800,23 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             }
             V.ostart[343] = (int64_t)pS.size();
             V.np = (int64_t)pS.size();
-            // offsets sorted by pair count are cut into kBuckets groups; each
-            // offset of a group owns a slab of the group's largest pair count
-            // (zero-padded), so one batched GEMM per group covers it
+            // offsets that occur, by decreasing pair count; the grouping into
+            // batched GEMMs (buckets) is chosen after the operators exist
             std::vector<int> ord;
             for (int o = 0; o < 343; ++o)
                 if (V.ostart[o + 1] > V.ostart[o]) ord.push_back(o);
             std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
                 return V.ostart[a + 1] - V.ostart[a] > V.ostart[b + 1] - V.ostart[b];
             });
-            std::vector<int64_t> colbase(343, 0), pcol(V.np);
-            V.buckets.clear();
-            int64_t col = 0;
-            const int nbk = std::min<int>(kBuckets, (int)ord.size());
-            for (int bk = 0; bk < nbk; ++bk) {
-                size_t lo = ord.size() * bk / nbk, hi = ord.size() * (bk + 1) / nbk;
-                FmmBucket B;
-                B.first = (int)lo;
-                B.count = (int)(hi - lo);
-                B.n = V.ostart[ord[lo] + 1] - V.ostart[ord[lo]];
-                for (size_t t = lo; t < hi; ++t) {
-                    colbase[ord[t]] = col;
-                    col += B.n;
-                }
-                V.buckets.push_back(B);
-            }
-            V.ncol = std::max<int64_t>(col, 1);
-            for (int o = 0; o < 343; ++o)
-                for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = colbase[o] + (t - V.ostart[o]);
             V.ord = ord;
-            V.colbase = colbase;
-            std::vector<int64_t> ooff(V.nc + 1, 0);
-            for (int32_t O : pO) ooff[O + 1]++;
-            for (int O = 0; O < V.nc; ++O) ooff[O + 1] += ooff[O];
-            std::vector<int64_t> oidx(V.np), fill(ooff.begin(), ooff.end() - 1);
-            for (int64_t t = 0; t < V.np; ++t) oidx[fill[pO[t]]++] = pcol[t];
+            V.hpO = pO;
+            V.hpS = pS;
+            m2l_layout(V, 1);  // the widest layout sizes the buffers
+            size_t ncol = (size_t)V.ncol;
             F_TRY(falloc(c, &V.pS, (size_t)V.np));
             F_TRY(falloc(c, &V.pcol, (size_t)V.np));
             F_TRY(falloc(c, &V.ooff, (size_t)V.nc + 1));
             F_TRY(falloc(c, &V.oidx, (size_t)V.np));
-            F_TRY(cudaMemcpyAsync(V.pS, pS.data(), V.np * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
-            F_TRY(cudaMemcpyAsync(V.pcol, pcol.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
-            F_TRY(cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
-            F_TRY(cudaMemcpyAsync(V.oidx, oidx.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
-            size_t ncol = (size_t)V.ncol;
             if (c->split) {
                 F_TRY(falloc(c, &V.Bbuf32, ncol * P));
                 F_TRY(falloc(c, &V.Cbuf32, ncol * F.nblk * P));
@@ -772,6 +853,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             }
         }
         V.Tlen = c->P.c * Tdt;
+        if (V.np > 0) F_TRY(m2l_tune_and_finalize(c, V));
     }
     return cudaStreamSynchronize(c->s);
 }
@@ -802,35 +884,17 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
             const int R = F.nblk * P;
             cudaEvent_t ev;
             phase_begin(c, &ev);
-            cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
-            const long long sA = (long long)R * P;
+            cublasStatus_t st;
             if (c->split) {
                 // FP32 operands, FP32-accurate products on the BF16 tensor
                 // cores (three BF16 terms per operand), FP64 locals
                 k_m2l_gather<float><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf32);
-                const float one = 1.0f, zero = 0.0f;
-                for (const FmmBucket &B : V.buckets) {
-                    if (st != CUBLAS_STATUS_SUCCESS) break;
-                    int64_t cb = V.colbase[V.ord[B.first]];
-                    st = cublasGemmStridedBatchedEx(
-                        F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one, V.op32 + (size_t)B.first * sA,
-                        CUDA_R_32F, P, sA, V.Bbuf32 + (size_t)cb * P, CUDA_R_32F, P, (long long)B.n * P, &zero,
-                        V.Cbuf32 + (size_t)cb * R, CUDA_R_32F, R, (long long)B.n * R, B.count,
-                        CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
-                }
+                st = m2l_gemms(c, V);
                 k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf32,
                                                          V.ring, V.G);
             } else {
                 k_m2l_gather<double><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf);
-                const double one = 1.0, zero = 0.0;
-                for (const FmmBucket &B : V.buckets) {
-                    if (st != CUBLAS_STATUS_SUCCESS) break;
-                    int64_t cb = V.colbase[V.ord[B.first]];
-                    st = cublasDgemmStridedBatched(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one,
-                                                   V.op + (size_t)B.first * sA, P, sA, V.Bbuf + (size_t)cb * P, P,
-                                                   (long long)B.n * P, &zero, V.Cbuf + (size_t)cb * R, R,
-                                                   (long long)B.n * R, B.count);
-                }
+                st = m2l_gemms(c, V);
                 k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf,
                                                           V.ring, V.G);
             }

@@ -5,7 +5,7 @@
 namespace tdbem {
 
 constexpr int kNearThreads = 128;
-constexpr int kUnroll = 4;  // window slots whose loads are issued together
+constexpr int kUnroll = 8;  // window slots whose loads are issued together
 
 // Incident-wave term e_i(t_a) of the total-field equation: u_in (OBIE) or
 // (d/dn_x - c^-1 d/dt) u_in (BMBIE) for the plane pulse

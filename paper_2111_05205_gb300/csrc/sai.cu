@@ -46,15 +46,23 @@ __device__ __forceinline__ double a_entry(int j, int l, int ns, int ell_w, const
 }
 
 // Slots of row i in the canonical order: the diagonal, then off-diagonal
-// entries with |A_ij| >= 1e-12 |A_ii| by decreasing magnitude (ties by
-// column).  Features of slot k (column j): A_ij/A_ii, A_jj/A_ii, A_ji/A_ii,
+// entries with |A_ij| >= 1e-12 |A_ii| by decreasing magnitude quantised to
+// 2^-20 of |A_ii| (ties by column), so that entries equal up to rounding --
+// common on symmetric meshes -- keep one order on every implementation.  Features of slot k (column j): A_ij/A_ii, A_jj/A_ii, A_ji/A_ii,
 // |x_i - x_j|/(c dt), 1.
+__device__ __forceinline__ long long sai_key(double v, double ainv_i)
+{
+    return (long long)floor(fabs(v * ainv_i) * 1048576.0);
+}
+
 __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, const int32_t *acol,
                         const double *ainv, const double *xc, double cdt, SaiRow &R)
 {
     double ad = 1.0 / ainv[i];
     int cols[kSaiMaxW];
     double vals[kSaiMaxW];
+    long long keys[kSaiMaxW];
+    keys[0] = 0;
     int n = 0;
     cols[n] = i;
     vals[n++] = ad;
@@ -63,14 +71,17 @@ __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, con
         if (j < 0) continue;
         double v = aoff[(int64_t)k * ns + i];
         if (!(fabs(v) >= 1e-12 * fabs(ad))) continue;
+        long long kv = sai_key(v, ainv[i]);
         int p = n++;
-        while (p > 1 && (fabs(vals[p - 1]) < fabs(v) || (fabs(vals[p - 1]) == fabs(v) && cols[p - 1] > j))) {
+        while (p > 1 && (keys[p - 1] < kv || (keys[p - 1] == kv && cols[p - 1] > j))) {
             vals[p] = vals[p - 1];
             cols[p] = cols[p - 1];
+            keys[p] = keys[p - 1];
             --p;
         }
         vals[p] = v;
         cols[p] = j;
+        keys[p] = kv;
     }
     R.n = n;
     R.inv_diag = ainv[i];
@@ -92,7 +103,17 @@ __device__ void sai_row(int i, int ns, int ell_w, int W, const double *aoff, con
     }
 }
 
-// Forward pass of one row: hidden activations h and outputs o.
+// Analytic part of the SAI row: Jacobi on the diagonal and the first
+// Neumann term -A_ij/(A_ii A_jj) off it, in units of 1/A_ii (the network
+// learns a correction to it).
+__device__ __forceinline__ float sai_base(int k, const float *f)
+{
+    if (f[kSaiF * k + 4] == 0.f) return 0.f;
+    return k == 0 ? 1.f : -f[kSaiF * k] / f[kSaiF * k + 1];
+}
+
+// Forward pass of one row: hidden activations h and outputs o (including
+// the analytic part).
 __device__ void sai_forward(int W, int H, const __half *w1, const __half *b1, const __half *w2, const __half *b2,
                             const float *in, float *h, float *o)
 {
@@ -105,7 +126,7 @@ __device__ void sai_forward(int W, int H, const __half *w1, const __half *b1, co
     for (int k = 0; k < W; ++k) {
         float s = __half2float(b2[k]);
         for (int a = 0; a < H; ++a) s += __half2float(w2[k * H + a]) * h[a];
-        o[k] = s;
+        o[k] = s + sai_base(k, in);
     }
 }
 
@@ -299,8 +320,9 @@ int tdbem_sai_create(int32_t width, int32_t hidden, uint64_t seed, tdbem_sai **o
     for (int e = 0; e < hidden * F; ++e) w[e] = a1 * (2.f * (float)((splitmix(st) >> 11) * 0x1.0p-53) - 1.f);
     for (int e = 0; e < width * hidden; ++e)
         w[hidden * F + hidden + e] = a2 * (2.f * (float)((splitmix(st) >> 11) * 0x1.0p-53) - 1.f);
-    // start from Jacobi: the output of the diagonal slot biased to 1 (M_ii = 1/A_ii)
-    w[hidden * F + hidden + width * hidden + 0] = 1.f;
+    // the output layer starts small: M starts at the analytic first-order
+    // Neumann SAI
+    for (int e = 0; e < width * hidden; ++e) w[hidden * F + hidden + e] *= 0.01f;
     std::vector<__half> w16(S->nw);
     for (int e = 0; e < S->nw; ++e) w16[e] = __float2half(w[e]);
     bool ok = cudaMalloc(&S->w, S->nw * sizeof(float)) == cudaSuccess &&

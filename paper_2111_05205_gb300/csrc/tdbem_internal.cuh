@@ -74,6 +74,9 @@ struct FmmLevel {
     std::vector<int> ord;        // offsets with pairs, by decreasing pair count
     std::vector<int64_t> colbase;  // [343] first column of each offset's slab
     std::vector<FmmBucket> buckets;
+    int nbk = 1;                 // buckets chosen by the autotuner
+    std::vector<std::pair<int, float>> tune;  // (buckets, ms) measured at setup
+    std::vector<int32_t> hpO, hpS;            // host copies of the pairs until the layout is final
     int64_t *pcol = nullptr;     // [np] padded column of each pair
     int64_t *ooff = nullptr;     // [nc+1] pairs of each observation cell (CSR)
     int64_t *oidx = nullptr;     // [np] their padded columns

@@ -58,15 +58,18 @@ def test_learned_sai_beats_jacobi_on_a_held_out_mesh():
         train.append(gpu_solver(workload("ellipsoid%d_bmbie_d2_hard_plane_s%d" % (ns, seed), nt=2)))
     sai = abi.tdbem_sai_create(12, 32, 3)
     try:
-        L0 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 1, 0.0)
-        L1 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 150, 2e-3)
-        assert L1 < 0.5 * L0, (L0, L1)
         w = workload("ellipsoid1280_bmbie_d2_hard_plane_s99", nt=30)
-        a, b = gpu_solver(w), gpu_solver(w)
+        a, b, c0 = gpu_solver(w), gpu_solver(w), gpu_solver(w)
         try:
             kj = a.stats()["solve_iters"]
+            use0, sweeps0, q0 = abi.tdbem_set_precond(c0.ctx, sai)  # untrained: the analytic part
+            L0 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 1, 0.0)
+            L1 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 150, 2e-3)
+            assert L1 < L0, (L0, L1)
             use, sweeps, q = abi.tdbem_set_precond(b.ctx, sai)
-            assert use and sweeps < kj, (use, sweeps, q, kj)
+            print("zero-lag sweeps: Jacobi %d, untrained SAI %d (q %.2e), trained SAI %d (q %.2e); loss %.3e -> %.3e"
+                  % (kj, sweeps0, q0, sweeps, q, L0, L1))
+            assert use and sweeps < kj and sweeps <= sweeps0, (use, sweeps, q, kj, sweeps0, q0)
             abi.tdbem_step(a.ctx, 29)
             abi.tdbem_step(b.ctx, 29)
             ua, _ = a.solution()
@@ -75,6 +78,7 @@ def test_learned_sai_beats_jacobi_on_a_held_out_mesh():
         finally:
             a.close()
             b.close()
+            c0.close()
     finally:
         abi.tdbem_sai_destroy(sai)
         for t in train:
