@@ -274,32 +274,34 @@ def run_ours(args):
     out["gpu_launches"] = int(launches)
 
     if fmm:
-        # accuracy: the direct path (parity-checked against the FP64 oracle)
-        # over the same steps, and the FMM's FP64 form
-        d = make("split", False)
-        abi.tdbem_step(d.ctx, spin)
-        Xd = _unknown(d, w, spin)
-        d.close()
-        X = X[:spin]
-        out["accuracy"] = {"rel_l2_vs_direct": float(np.linalg.norm(X - Xd) / np.linalg.norm(Xd)),
-                           "steps": spin, "target": 1e-3,
-                           "reference": "direct history sum, parity 1e-11 with the FP64 oracle"}
-        if args.fp64_form and args.precision != "fp64":
-            f64 = make("fp64", True)
-            abi.tdbem_step(f64.ctx, spin)
-            Xf = _unknown(f64, w, spin)
-            abi.tdbem_reset_stats(f64.ctx)
-            msf = _timed(abi, torch, f64.ctx, min(args.steps, 40))
-            f64.close()
-            out["fp64_form"] = {"value": 1000.0 * min(args.steps, 40) / msf, "unit": "time-steps/s",
-                                "rel_l2_vs_direct": float(np.linalg.norm(Xf - Xd) / np.linalg.norm(Xd))}
-        if args.direct_form:
-            dd = make("split", False)
-            abi.tdbem_step(dd.ctx, spin)
-            msd = _timed(abi, torch, dd.ctx, args.steps)
-            dd.close()
-            out["direct_form"] = {"value": 1000.0 * args.steps / msd, "unit": "time-steps/s",
-                                  "precision": "split", "note": "exact path (no FMM), all element pairs"}
+        if args.accuracy:
+            # accuracy: the direct path (parity-checked against the FP64 oracle)
+            # over the same steps, and the FMM's FP64 form
+            d = make("split", False)
+            abi.tdbem_step(d.ctx, spin)
+            Xd = _unknown(d, w, spin)
+            d.close()
+            X = X[:spin]
+            out["accuracy"] = {"rel_l2_vs_direct": float(np.linalg.norm(X - Xd) / np.linalg.norm(Xd)),
+                               "steps": spin, "target": 1e-3,
+                               "reference": "direct history sum, parity 1e-11 with the FP64 oracle"}
+            if args.fp64_form and args.precision != "fp64":
+                f64 = make("fp64", True)
+                abi.tdbem_step(f64.ctx, spin)
+                Xf = _unknown(f64, w, spin)
+                abi.tdbem_reset_stats(f64.ctx)
+                msf = _timed(abi, torch, f64.ctx, min(args.steps, 40))
+                f64.close()
+                out["fp64_form"] = {"value": 1000.0 * min(args.steps, 40) / msf, "unit": "time-steps/s",
+                                    "rel_l2_vs_direct": float(np.linalg.norm(Xf - Xd) / np.linalg.norm(Xd)),
+                                    "mixed_rel_l2_vs_this": float(np.linalg.norm(X - Xf) / np.linalg.norm(Xf))}
+            if args.direct_form:
+                dd = make("split", False)
+                abi.tdbem_step(dd.ctx, spin)
+                msd = _timed(abi, torch, dd.ctx, args.steps)
+                dd.close()
+                out["direct_form"] = {"value": 1000.0 * args.steps / msd, "unit": "time-steps/s",
+                                      "precision": "split", "note": "exact path (no FMM), all element pairs"}
     else:
         if args.fp64_form and args.precision != "fp64":
             out["fp64_form"] = fp64_form(args, w, phi, stream)
@@ -320,15 +322,26 @@ def run_ours(args):
             Xf = _unknown(f, w, n_done)
             f.close()
             m2l_tf = stf["m2l_flops"] / (stf["ms_m2l"] * 1e-3) / 1e12 if stf["ms_m2l"] > 0 else 0.0
-            err = [float(np.linalg.norm(Xf[:n] - X[:n]) / np.linalg.norm(X[:n])) for n in (60, 120, 240, n_done)
-                   if n <= n_done]
+            marks = [n for n in (60, 120, 240, n_done) if n <= n_done]
+            err = [float(np.linalg.norm(Xf[:n] - X[:n]) / np.linalg.norm(X[:n])) for n in marks]
+            # the same FMM with every pass in FP64: the mixed form's own error
+            f64 = make("fp64", True)
+            abi.tdbem_step(f64.ctx, n_done)
+            X64 = _unknown(f64, w, n_done)
+            f64.close()
+            err64 = [float(np.linalg.norm(Xf[:n] - X64[:n]) / np.linalg.norm(X64[:n])) for n in marks]
+            err64d = [float(np.linalg.norm(X64[:n] - X[:n]) / np.linalg.norm(X[:n])) for n in marks]
             out["fmm_form"] = {"value": 1000.0 * args.steps / msf, "unit": "time-steps/s",
                                "config": "depth %d, ps=pt=%d, mu=%d, Lt=%d, %s" % (
                                    args.depth, args.ps, stf["fmm_mu"], stf["fmm_lt"],
                                    "M2L FP32 on tensor cores (BF16x9)" if args.precision != "fp64" else "FP64"),
                                "rel_l2_vs_direct_after_steps": dict(zip([str(n) for n in (60, 120, 240, n_done)
                                                                          if n <= n_done], err)),
-                               "meets_1e-3": bool(max(err) <= 1e-3), "m2l_tflops": m2l_tf,
+                               "meets_1e-3": bool(max(err) <= 1e-3),
+                               "mixed_vs_fp64_fmm_after_steps": dict(zip([str(n) for n in marks], err64)),
+                               "mixed_meets_1e-3_vs_fp64_fmm": bool(max(err64) <= 1e-3),
+                               "fp64_fmm_vs_direct_after_steps": dict(zip([str(n) for n in marks], err64d)),
+                               "m2l_tflops": m2l_tf,
                                "m2l_ms_per_step": stf["ms_m2l"] / args.steps,
                                "near_ms_per_step": stf["ms_near"] / args.steps,
                                "far_ms_per_step": stf["ms_far"] / args.steps, "setup_s": round(fsetup, 2),
@@ -404,31 +417,60 @@ def _kernel_rev():
     return h.hexdigest()[:12]
 
 
-def cpu_baseline(w, rows=4, repeats=3):
-    """The FP64 oracle on the host cores, on a bounded sample of the
-    workload: the history sum of ``rows`` observation rows over every lag
-    and every source element (its step loop, Eq. linear, restricted to those
-    rows), scaled to all Ns rows; the rows' coefficients are the oracle's
-    (computed first, untimed)."""
-    from oracle import coeffs as oc
-    cdt = w.c * w.dt
-    gm = oc.gamma_max(w.xyz, w.tri, w.d, cdt)
-    rng = np.random.default_rng(0)
-    rsel = np.sort(rng.choice(w.ns, size=rows, replace=False))
-    kind = "wb" if w.bc == "neumann" else "ub"
-    C = oc.rows(w.xyz, w.tri, w.d, cdt, rsel, kinds=(kind,), gmax=gm)[kind]  # [r, g, j]
-    hist = np.random.default_rng(1).standard_normal((gm + 1, w.ns))
-    ts = []
-    for _ in range(repeats):
+class _OracleSample:
+    """The FP64 oracle on the host cores on a bounded sample of the
+    workload: the history sum (its step loop, Eq. linear) of `rows`
+    observation rows over every lag and every source element; the rows'
+    coefficients are the oracle's (computed once, untimed); one step of the
+    sample is scaled by Ns / rows to a full step."""
+
+    def __init__(self, w, rows):
+        from oracle import coeffs as oc
+        cdt = w.c * w.dt
+        self.gm = oc.gamma_max(w.xyz, w.tri, w.d, cdt)
+        rng = np.random.default_rng(0)
+        self.rows = np.sort(rng.choice(w.ns, size=rows, replace=False))
+        kind = "wb" if w.bc == "neumann" else "ub"
+        self.C = oc.rows(w.xyz, w.tri, w.d, cdt, self.rows, kinds=(kind,), gmax=self.gm)[kind]  # [r, g, j]
+        self.hist = np.random.default_rng(1).standard_normal((self.gm + 1, w.ns))
+        self.ns = w.ns
+        self.cores = oc.num_threads()
+        self.sample = ("history sum of %d of %d rows over all %d lags (oracle dense rows, numpy), scaled x%.0f"
+                       % (rows, w.ns, self.gm, w.ns / rows))
+
+    def step_seconds(self):
         t = time.perf_counter()
-        b = np.zeros(rows)
-        for g in range(1, gm + 1):
-            b += C[:, g, :] @ hist[gm - g]
-        ts.append(time.perf_counter() - t)
-    per_step = min(ts) * w.ns / rows
-    return {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": oc.num_threads(), "kind": "oracle",
-            "sample": "history sum of %d of %d rows over all %d lags (oracle dense rows, numpy), scaled x%.0f"
-                      % (rows, w.ns, gm, w.ns / rows)}
+        b = np.zeros(len(self.rows))
+        for g in range(1, self.gm + 1):
+            b += self.C[:, g, :] @ self.hist[self.gm - g]
+        return (time.perf_counter() - t) * self.ns / len(self.rows)
+
+
+def cpu_baseline(w, rows=2, repeats=3):
+    o = _OracleSample(w, rows)
+    per_step = min(o.step_seconds() for _ in range(repeats))
+    return {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": o.cores, "kind": "oracle", "sample": o.sample}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import workload
+    w = workload(args.workload)
+    o = _OracleSample(w, args.cpu_rows)
+    for _ in range(args.warmup):
+        o.step_seconds()
+    per_step = float(np.mean([o.step_seconds() for _ in range(args.steps)]))
+    out = {"metric": METRIC, "value": 1.0 / per_step, "unit": "time-steps/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload + "_direct_fp64", "ns": w.ns},
+           "cpu_baseline": {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": o.cores,
+                            "kind": "oracle", "sample": o.sample},
+           "e2e": {"value": 1.0 / per_step, "unit": "time-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
 
 
 def run_batch(args):
@@ -484,30 +526,6 @@ def run_batch(args):
                       "timing": "host clock around each mode, device synchronised"}))
 
 
-def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    from synth import workload
-    w = workload(args.workload)
-    rows = args.cpu_rows
-    samples = []
-    for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, rows=rows, repeats=1)
-        if k >= args.warmup:
-            samples.append(1.0 / cb["value"])
-    per_step = float(np.mean(samples))
-    out = {"metric": METRIC, "value": 1.0 / per_step, "unit": "time-steps/s", "n_gpus": 0,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD + "_direct_fp64", "ns": w.ns},
-           "cpu_baseline": {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": cb["cores"],
-                            "kind": "oracle", "sample": cb["sample"]},
-           "e2e": {"value": 1.0 / per_step, "unit": "time-steps/s", "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -525,6 +543,8 @@ def main():
     ap.add_argument("--pt", type=int, default=4)
     ap.add_argument("--direct-form", action="store_true")
     ap.add_argument("--no-fmm-form", dest="fmm_form", action="store_false")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                    help="--algo fmm: skip the comparison runs against the direct path and the FP64 form")
     ap.add_argument("--batch", type=int, default=0, help="measure the batched driver with N instances")
     args = ap.parse_args()
     if args.warmup < 3:

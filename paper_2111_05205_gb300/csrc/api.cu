@@ -406,12 +406,17 @@ int tdbem_prepare(tdbem_ctx *c)
     if (K > maxit) return fail(c, TDBEM_ERR_NOT_CONVERGED, "zero-lag solve needs more sweeps than solver_maxit");
     c->solve_iters = K;
 
-    // histories, initialised with the known data (unknown components zero)
+    // histories, initialised with the known data (unknown components zero).
+    // Each is preceded by gmax zero rows: a lag g of step alpha reads row
+    // alpha - g >= 1 - gmax, so the history sum needs no range test.
     size_t nh = (size_t)nt * ns;
-    TD_CUDA(dalloc(c, &c->d_u, nh));
-    TD_CUDA(dalloc(c, &c->d_q, nh));
-    TD_CUDA(cudaMemsetAsync(c->d_u, 0, nh * sizeof(double), c->s));
-    TD_CUDA(cudaMemsetAsync(c->d_q, 0, nh * sizeof(double), c->s));
+    const size_t npad = (size_t)c->gmax * ns;
+    TD_CUDA(dalloc(c, &c->d_u, npad + nh));
+    TD_CUDA(dalloc(c, &c->d_q, npad + nh));
+    TD_CUDA(cudaMemsetAsync(c->d_u, 0, (npad + nh) * sizeof(double), c->s));
+    TD_CUDA(cudaMemsetAsync(c->d_q, 0, (npad + nh) * sizeof(double), c->s));
+    c->d_u += npad;
+    c->d_q += npad;
     if (has_k) {
         double *d_f = nullptr;
         TD_CUDA(dalloc(c, &d_f, (size_t)(nt - 1) * ns));
@@ -422,8 +427,12 @@ int tdbem_prepare(tdbem_ctx *c)
         dfree(c, d_f);
     }
     if (c->split) {
-        TD_CUDA(dalloc(c, &c->d_us, nh));
-        TD_CUDA(dalloc(c, &c->d_qs, nh));
+        TD_CUDA(dalloc(c, &c->d_us, npad + nh));
+        TD_CUDA(dalloc(c, &c->d_qs, npad + nh));
+        TD_CUDA(cudaMemsetAsync(c->d_us, 0, npad * sizeof(float2), c->s));
+        TD_CUDA(cudaMemsetAsync(c->d_qs, 0, npad * sizeof(float2), c->s));
+        c->d_us += npad;
+        c->d_qs += npad;
         TD_CUDA(launch_split_histories(c));
         TD_CUDA(launch_split_coefficients(c));
     }

@@ -5,7 +5,9 @@
 namespace tdbem {
 
 constexpr int kNearThreads = 128;
-constexpr int kUnroll = 8;  // window slots whose loads are issued together
+constexpr int kUnroll = 8;  // full window slots whose loads are issued together
+constexpr int kMaxFull = 6;       // full window slots handled by the unrolled bodies
+constexpr int kNearPrefetch = 2;  // blocks of a warp whose coefficients are asked of L2 ahead
 
 // Incident-wave term e_i(t_a) of the total-field equation: u_in (OBIE) or
 // (d/dn_x - c^-1 d/dt) u_in (BMBIE) for the plane pulse
@@ -54,36 +56,181 @@ __device__ __forceinline__ void df_renorm(DF &a)
     a.h = s;
 }
 
-// b_i = -e_i - sum_j sum_{g in window(i,j), g <= a} (KU^(g)_ij q_j^{a-g} - KW^(g)_ij u_j^{a-g})
-// One CTA per row i; each warp walks 32-pair blocks of the row.  Window
-// slot s of a block is stored packed (lanes with cnt > s, in lane order),
-// so every load of the coefficient stream is a contiguous warp access; the
-// history entries x_j^{a-g} of one slot differ only by the lanes' g0.
-// The row sum is reduced in a fixed order (deterministic).
-// SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
-// coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
-// are read from their float-pair copies and the sum runs in double-float.
-template <bool HU, bool HW, bool SPLIT>
-__global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
-                                                              const int64_t *__restrict__ prow,
-                                                           const int32_t *__restrict__ col,
-                                                           const int64_t *__restrict__ rowblk,
-                                                           const uint16_t *__restrict__ meta,
-                                                           const int64_t *__restrict__ boff,
-                                                           const double *__restrict__ ku,
-                                                           const double *__restrict__ kw,
-                                                           const double *__restrict__ u_,
-                                                           const double *__restrict__ q,
-                                                           const float2 *__restrict__ us,
-                                                           const float2 *__restrict__ qs,
-                                                           const double *__restrict__ exc, Incident inc,
-                                                           const double *__restrict__ xc,
-                                                           const double *__restrict__ nrm,
-                                                           const double *__restrict__ far, double *b)
+// Element types of the history sum: FP64, or a float pair (hi, lo) in the
+// same 8 bytes for the split form.
+template <bool SPLIT>
+struct NearV {
+    using T = double;
+};
+template <>
+struct NearV<true> {
+    using T = float2;
+};
+
+template <bool SPLIT, bool NEG>
+__device__ __forceinline__ void near_fma(DF &dacc, double &acc, const typename NearV<SPLIT>::T &c,
+                                         const typename NearV<SPLIT>::T &x)
 {
-    __shared__ double red[kNearThreads / 32];
-    if (alpha_dev) alpha = *alpha_dev;
-    const int i = blockIdx.x;
+    if constexpr (SPLIT) {
+        if (NEG)
+            df_fma(dacc, -c.x, -c.y, x.x, x.y);
+        else
+            df_fma(dacc, c.x, c.y, x.x, x.y);
+    } else {
+        if (NEG)
+            acc = fma(-c, x, acc);
+        else
+            acc = fma(c, x, acc);
+    }
+}
+
+// One 32-pair block of a row: lane l holds pair (i, j_l) whose window is
+// lags g0_l .. g0_l + cnt_l - 1.  Slot s of the block is stored packed (the
+// lanes with cnt > s, in lane order) from offset o.  The N slots below the
+// block's smallest count hold all 32 lanes, so lane l of slot s sits at
+// o + 32 s + l; the first tail slot (s = N, lanes with cnt > N) is located
+// by a ballot.  N is a template constant, so neither the full slots nor the
+// loads carry a per-slot test, and the loads of all N + 1 slots are issued
+// before any is used.  (In typical windows the counts of a block differ by
+// at most one, so this covers every slot of nearly every block.)  In the
+// early steps a lag can reach before the first step (beta < 0): the
+// histories are allocated with as many zero rows before step 0 as the
+// largest stored lag, so those terms read zeros and add nothing.
+template <bool HU, bool HW, bool SPLIT, int N>
+__device__ __forceinline__ void near_slots(const typename NearV<SPLIT>::T *__restrict__ kub,
+                                           const typename NearV<SPLIT>::T *__restrict__ kwb,
+                                           const typename NearV<SPLIT>::T *__restrict__ hqb,
+                                           const typename NearV<SPLIT>::T *__restrict__ hub, int ns, int lane,
+                                           unsigned lt, int cnt, bool tail, DF &dacc, double &acc)
+{
+    using V = typename NearV<SPLIT>::T;
+    V cu[N + 1], xu[N + 1], cw[N + 1], xw[N + 1];
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        if (HU) {
+            cu[s] = __ldcs(kub + 32 * s + lane);
+            xu[s] = *(hqb - (int64_t)s * ns);
+        }
+        if (HW) {
+            cw[s] = __ldcs(kwb + 32 * s + lane);
+            xw[s] = *(hub - (int64_t)s * ns);
+        }
+    }
+    bool on = false;
+    if (tail) {  // warp-uniform
+        const unsigned mask = __ballot_sync(0xffffffffu, cnt > N);
+        on = cnt > N;
+        if (on) {
+            const int idx = 32 * N + __popc(mask & lt);
+            if (HU) {
+                cu[N] = __ldcs(kub + idx);
+                xu[N] = *(hqb - (int64_t)N * ns);
+            }
+            if (HW) {
+                cw[N] = __ldcs(kwb + idx);
+                xw[N] = *(hub - (int64_t)N * ns);
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        if (HU) near_fma<SPLIT, true>(dacc, acc, cu[s], xu[s]);
+        if (HW) near_fma<SPLIT, false>(dacc, acc, cw[s], xw[s]);
+    }
+    if (on) {
+        if (HU) near_fma<SPLIT, true>(dacc, acc, cu[N], xu[N]);
+        if (HW) near_fma<SPLIT, false>(dacc, acc, cw[N], xw[N]);
+    }
+}
+
+// Slots s0 <= s < cmax of a block, one at a time, each located by a ballot
+// (blocks whose counts differ by more than one, or exceed the unrolled
+// range).
+template <bool HU, bool HW, bool SPLIT>
+__device__ __forceinline__ void near_slots_rest(const typename NearV<SPLIT>::T *__restrict__ kub,
+                                             const typename NearV<SPLIT>::T *__restrict__ kwb,
+                                             const typename NearV<SPLIT>::T *__restrict__ hqb,
+                                             const typename NearV<SPLIT>::T *__restrict__ hub, int ns, int lane,
+                                             unsigned lt, int cnt, int s0, int cmin, int cmax, DF &dacc,
+                                             double &acc)
+{
+    using V = typename NearV<SPLIT>::T;
+    // offset of slot s0: full slots hold 32 entries, tail slots their lanes
+    int pos = 32 * min(s0, cmin);
+    for (int s = cmin; s < s0; ++s) pos += __popc(__ballot_sync(0xffffffffu, cnt > s));
+    for (int s = s0; s < cmax; ++s) {
+        const unsigned mask = __ballot_sync(0xffffffffu, cnt > s);
+        if (cnt > s) {
+            const int idx = pos + __popc(mask & lt);
+            const int64_t h = (int64_t)s * ns;
+            if (HU) near_fma<SPLIT, true>(dacc, acc, __ldcs(kub + idx), *(hqb - h));
+            if (HW) near_fma<SPLIT, false>(dacc, acc, __ldcs(kwb + idx), *(hub - h));
+        }
+        pos += __popc(mask);
+    }
+}
+
+template <bool HU, bool HW, bool SPLIT>
+__device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__restrict__ kub,
+                                           const typename NearV<SPLIT>::T *__restrict__ kwb,
+                                           const typename NearV<SPLIT>::T *__restrict__ hqb,
+                                           const typename NearV<SPLIT>::T *__restrict__ hub, int cnt, int ns,
+                                           int lane, unsigned lt, DF &dacc, double &acc)
+{
+    const int cmin = (int)__reduce_min_sync(0xffffffffu, (unsigned)cnt);
+    const int cmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    const bool tail = cmax > cmin;
+    // both kinds at once keep twice the values per slot in registers
+    constexpr int MF = (HU && HW) ? kMaxFull / 2 : kMaxFull;
+    const int nf = cmin < MF ? cmin : MF;
+#define TDBEM_NEAR_CASE(n)                                                                                     \
+    case n:                                                                                                    \
+        if constexpr (n <= MF) near_slots<HU, HW, SPLIT, n>(kub, kwb, hqb, hub, ns, lane, lt, cnt, tail, dacc, acc); \
+        break;
+    switch (nf) {  // warp-uniform
+        TDBEM_NEAR_CASE(0)
+        TDBEM_NEAR_CASE(1)
+        TDBEM_NEAR_CASE(2)
+        TDBEM_NEAR_CASE(3)
+        TDBEM_NEAR_CASE(4)
+        TDBEM_NEAR_CASE(5)
+        TDBEM_NEAR_CASE(6)
+    }
+#undef TDBEM_NEAR_CASE
+    // slots the unrolled bodies did not reach
+    const int done = nf + (tail ? 1 : 0);
+    if (done < cmax)
+        near_slots_rest<HU, HW, SPLIT>(kub, kwb, hqb, hub, ns, lane, lt, cnt, done, cmin, cmax, dacc, acc);
+}
+
+// Asks L2 to fetch the coefficient bytes [a, e) of a block ahead of its
+// use, so the warp's own loads wait for an L2 hit rather than HBM.
+__device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_t e, int lane)
+{
+    const size_t end = __cvta_generic_to_global(k + e);
+    const size_t p = (__cvta_generic_to_global(k + a) & ~(size_t)127) + 128 * (size_t)lane;
+    if (p < end) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <bool HU, bool HW, bool SPLIT>
+__device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t *__restrict__ prow,
+                                         const int32_t *__restrict__ col, const int64_t *__restrict__ rowblk,
+                                         const uint16_t *__restrict__ meta, const int64_t *__restrict__ boff,
+                                         const double *__restrict__ ku, const double *__restrict__ kw,
+                                         const double *__restrict__ u_, const double *__restrict__ q,
+                                         const float2 *__restrict__ us, const float2 *__restrict__ qs, DF &dacc,
+                                         double &acc)
+{
+    using V = typename NearV<SPLIT>::T;
+    constexpr int W = kNearThreads / 32;
+    const V *hq, *hu;
+    if constexpr (SPLIT) {
+        hq = qs;
+        hu = us;
+    } else {
+        hq = q;
+        hu = u_;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t p0 = prow[i];
@@ -92,95 +239,87 @@ __global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha,
     const int32_t *crow = col ? col + p0 : nullptr;
     const int64_t *orow = boff + rowblk[i];
     const int nblk = (int)(rowblk[i + 1] - rowblk[i]);
-    double acc = 0.0;
-    DF dacc = {0.f, 0.f};
+    const V *kuv = reinterpret_cast<const V *>(ku);
+    const V *kwv = reinterpret_cast<const V *>(kw);
+    // the warp asks L2 for the coefficients of its block kNearPrefetch blocks
+    // ahead (here: of its first kNearPrefetch blocks)
+    for (int t = 0; t < kNearPrefetch; ++t) {
+        const int pb = warp + W * t;
+        if (pb < nblk) {
+            if (HU) near_prefetch(ku, orow[pb], orow[pb + 1], lane);
+            if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
+        }
+    }
     // metadata of the first block; the next block's is fetched while the
     // current one is summed
     int bk = warp;
     unsigned mnext = 0u;
     int64_t onext = 0;
     if (bk < nblk) {
-        int pr = bk * 32 + lane;
+        const int pr = bk * 32 + lane;
         mnext = (pr < npr) ? mrow[pr] : 0u;
         onext = orow[bk];
     }
-    for (; bk < nblk; bk += kNearThreads / 32) {
+    for (; bk < nblk; bk += W) {
+        {
+            const int pb = bk + W * kNearPrefetch;
+            if (pb < nblk) {
+                if (HU) near_prefetch(ku, orow[pb], orow[pb + 1], lane);
+                if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
+            }
+        }
         const int pr = bk * 32 + lane;
         const int j = (pr < npr) ? (crow ? crow[pr] : pr) : 0;
         const unsigned m = mnext;
-        int64_t pos = onext;
-        int nb = bk + kNearThreads / 32;
+        const int64_t o = onext;
+        const int nb = bk + W;
         if (nb < nblk) {
-            int pn = nb * 32 + lane;
+            const int pn = nb * 32 + lane;
             mnext = (pn < npr) ? mrow[pn] : 0u;
             onext = orow[nb];
         }
-        const int g0 = m & kMaxG0, cnt = m >> kG0Bits;  // cnt = 0 past the row's end
-        const int sm = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
-        // lag g = g0 + s reaches back to beta = alpha - g
-        const int beta0 = alpha - g0;
-        const int64_t h0 = (int64_t)beta0 * ns + j;
-        // groups of kUnroll window slots: every load of a group is issued
-        // before any of them is used
-        for (int s0 = 0; s0 < sm; s0 += kUnroll) {
-            int64_t idx[kUnroll];
-            bool act[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                int s = s0 + u;
-                unsigned mask = __ballot_sync(0xffffffffu, cnt > s);
-                act[u] = cnt > s && beta0 - s >= 0;
-                idx[u] = pos + __popc(mask & lt);
-                pos += __popc(mask);
-            }
-            if (SPLIT) {
-                float2 cu[kUnroll], xu[kUnroll], cw[kUnroll], xw[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    int64_t h = h0 - (int64_t)(s0 + u) * ns;
-                    if (act[u]) {
-                        if (HU) {
-                            cu[u] = __ldcs(reinterpret_cast<const float2 *>(ku) + idx[u]);
-                            xu[u] = qs[h];
-                        }
-                        if (HW) {
-                            cw[u] = __ldcs(reinterpret_cast<const float2 *>(kw) + idx[u]);
-                            xw[u] = us[h];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    if (act[u]) {
-                        if (HU) df_fma(dacc, -cu[u].x, -cu[u].y, xu[u].x, xu[u].y);
-                        if (HW) df_fma(dacc, cw[u].x, cw[u].y, xw[u].x, xw[u].y);
-                    }
-            } else {
-                double cu[kUnroll], xu[kUnroll], cw[kUnroll], xw[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    int64_t h = h0 - (int64_t)(s0 + u) * ns;
-                    if (act[u]) {
-                        if (HU) {
-                            cu[u] = __ldcs(ku + idx[u]);
-                            xu[u] = q[h];
-                        }
-                        if (HW) {
-                            cw[u] = __ldcs(kw + idx[u]);
-                            xw[u] = u_[h];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    if (act[u]) {
-                        if (HU) acc -= cu[u] * xu[u];
-                        if (HW) acc += cw[u] * xw[u];
-                    }
-            }
-        }
+        // cnt = 0 past the row's end; lag g = g0 + s reaches back to
+        // beta = alpha - g0 - s
+        const int g0 = (int)(m & kMaxG0), cnt = (int)(m >> kG0Bits);
+        const int64_t hb = (int64_t)(alpha - g0) * ns + j;
+        near_block<HU, HW, SPLIT>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
         if (SPLIT) df_renorm(dacc);
     }
+}
+
+// b_i = -e_i - sum_j sum_{g in window(i,j), g <= a} (KU^(g)_ij q_j^{a-g} - KW^(g)_ij u_j^{a-g})
+// One CTA per row i; each warp walks 32-pair blocks of the row; every load
+// of the coefficient stream is a contiguous warp access, and the history
+// entries x_j^{a-g} of one slot differ only by the lanes' g0.  The row sum
+// is reduced in a fixed order (deterministic).
+// SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
+// coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
+// are read from their float-pair copies and the sum runs in double-float.
+template <bool HU, bool HW, bool SPLIT>
+__global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
+                                                              const int64_t *__restrict__ prow,
+                                                              const int32_t *__restrict__ col,
+                                                              const int64_t *__restrict__ rowblk,
+                                                              const uint16_t *__restrict__ meta,
+                                                              const int64_t *__restrict__ boff,
+                                                              const double *__restrict__ ku,
+                                                              const double *__restrict__ kw,
+                                                              const double *__restrict__ u_,
+                                                              const double *__restrict__ q,
+                                                              const float2 *__restrict__ us,
+                                                              const float2 *__restrict__ qs,
+                                                              const double *__restrict__ exc, Incident inc,
+                                                              const double *__restrict__ xc,
+                                                              const double *__restrict__ nrm,
+                                                              const double *__restrict__ far, double *b)
+{
+    __shared__ double red[kNearThreads / 32];
+    if (alpha_dev) alpha = *alpha_dev;
+    const int i = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    DF dacc = {0.f, 0.f};
+    near_row<HU, HW, SPLIT>(i, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
     if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;

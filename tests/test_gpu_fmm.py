@@ -34,6 +34,11 @@ CASES = [
     ("ellipsoid320_bmbie_d2_hard_plane_s7", 2, 3, 37),
     ("sphere1280_obie_d1_dirichlet_uniform", 3, 2, 29),
     ("sphere1280_bmbie_d1_dirichlet_uniform", 3, 3, 22),
+    # long runs: the distant-future recurrence of Formula 1 is active (the
+    # observed interval lies far more than mu+1 intervals after the early
+    # source intervals)
+    ("ellipsoid320_bmbie_d2_hard_plane_s7", 2, 2, 81),
+    ("sphere1280_bmbie_d2_neumann_uniform", 3, 2, 81),
 ]
 
 
