@@ -367,15 +367,24 @@ FP64_TFLOPS = 1.19  # FP64 FMA-chain probe on this machine's GB300 (0.596 TFMA/s)
 
 
 def _traffic(st):
-    tr_path = os.path.join(ROOT, "profiles", "near_sum_traffic.json")
+    """DRAM bytes (read + write) of one history-sum launch, from the ncu
+    counters summarised in profiles/near_sum_traffic.txt: their ratio to the
+    algorithmic bytes on the capture's workload, times this launch's
+    algorithmic bytes.  None unless the summary is for the kernel as built
+    (same source revision)."""
+    tr_path = os.path.join(ROOT, "profiles", "near_sum_traffic.txt")
     if not os.path.exists(tr_path):
         return None
     try:
+        kv = {}
         with open(tr_path) as f:
-            tr = json.load(f)
-        if tr.get("kernel_rev") != _kernel_rev():
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_rev") != _kernel_rev():
             return None
-        return tr["bytes_per_algorithmic_byte"] * st["near_bytes_per_step"]
+        return float(kv["bytes_per_algorithmic_byte"]) * st["near_bytes_per_step"]
     except Exception:
         return None
 
@@ -474,55 +483,77 @@ def run_reference(args):
 
 
 def run_batch(args):
-    """Batched driver: N independent instances (seeded ellipsoids, Ns cycling
-    80 / 320 / 1280, d cycling 2 / 1, BMBIE, sound-hard, split precision),
-    each advanced `steps` steps by (a) plain launches, one instance after
-    another, (b) one graph per instance, (c) one graph for all instances."""
+    """Batched driver on a mix shaped like the batched workload: N independent
+    instances (seeded ellipsoids; Ns alternating 1280 / 5120; Nt drawn from
+    U{256..1024}; OBIE d=1 and BMBIE d=2 alternating; sound-hard; split
+    precision).  From the same start (a checkpoint after the warm-up steps)
+    every instance is marched to its own last step Nt-1 by (a) plain
+    launches, one instance after another, (b) one graph per instance, (c) one
+    graph for all instances, replayed until the longest is done (shorter ones
+    stop at their end on the device).  Timed with the host clock around each
+    mode, device synchronised."""
     import torch
     from paper_2111_05205_gb300 import abi, build
     from synth import workload
     from tests.gpu_cases import gpu_solver
     build.build()
-    n, k = args.batch, args.steps
-    ws = [workload("ellipsoid%d_bmbie_d%d_hard_plane_s%d" % ((80, 320, 1280)[i % 3], 1 if i % 2 else 2, i + 1),
-                   nt=3 * k + args.warmup + 3) for i in range(n)]
+    n = args.batch
+    rng = np.random.default_rng(2024)
+    nts = [int(v) for v in rng.integers(256, 1025, size=n)]
+    ws = [workload("ellipsoid%d_%s_hard_plane_s%d" % ((1280, 5120)[i % 2], ("bmbie_d2", "obie_d1")[(i // 2) % 2], i + 1),
+                   nt=nts[i]) for i in range(n)]
+    t0 = time.time()
     sols = [gpu_solver(w, precision=1) for w in ws]
+    setup_s = time.time() - t0
     try:
         for s in sols:
             abi.tdbem_step(s.ctx, args.warmup)
+        blobs = [abi.tdbem_checkpoint(s.ctx) for s in sols]
+        todo = [nt - 1 - args.warmup for nt in nts]
+        tot = sum(todo)
+
+        def reset():
+            for s, b in zip(sols, blobs):
+                abi.tdbem_restore(s.ctx, b)
+            torch.cuda.synchronize()
+
         torch.cuda.synchronize()
         t = time.perf_counter()
-        for s in sols:
-            abi.tdbem_step(s.ctx, k)
+        for s, m in zip(sols, todo):
+            abi.tdbem_step(s.ctx, m)
         torch.cuda.synchronize()
         t_plain = time.perf_counter() - t
-        for s in sols:
-            abi.tdbem_step_graph(s.ctx, 1)
-        torch.cuda.synchronize()
+        X_plain = [s.solution(0, nt - 1)[0] for s, nt in zip(sols, nts)]
+        reset()
         t = time.perf_counter()
-        for s in sols:
-            abi.tdbem_step_graph(s.ctx, k - 1)
+        for s, m in zip(sols, todo):
+            abi.tdbem_step_graph(s.ctx, m)
         torch.cuda.synchronize()
-        t_graph = (time.perf_counter() - t) * k / (k - 1)
+        t_graph = time.perf_counter() - t
+        reset()
         B = abi.tdbem_batch_create([s.ctx for s in sols])
         try:
-            abi.tdbem_batch_step(B, 1)
-            abi.tdbem_batch_sync(B)
             t = time.perf_counter()
-            abi.tdbem_batch_step(B, k - 1)
+            abi.tdbem_batch_step(B, max(todo))
             abi.tdbem_batch_sync(B)
-            t_batch = (time.perf_counter() - t) * k / (k - 1)
+            t_batch = time.perf_counter() - t
         finally:
             abi.tdbem_batch_destroy(B)
+        same = all(np.array_equal(s.solution(0, nt - 1)[0], x) for s, nt, x in zip(sols, nts, X_plain))
+        launches = sum(m * (1 + s.stats()["solve_iters"] + 1) for s, m in zip(sols, todo))
     finally:
         for s in sols:
             s.close()
-    tot = n * k
     print(json.dumps({"metric": "instance-steps/sec, batched driver", "value": tot / t_batch,
-                      "unit": "instance-steps/s", "n_gpus": 1, "steps": k, "warmup": args.warmup,
-                      "higher_is_better": True, "dtype": "f64+df32", "data": "synthetic",
-                      "config": {"workload": "batch%d_ellipsoids_ns80-320-1280_bmbie_d1-2" % n, "instances": n},
+                      "unit": "instance-steps/s", "n_gpus": 1, "steps": max(todo), "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
+                      "config": {"workload": "batch%d_ellipsoids_ns1280-5120_nt256-1024_obie-d1_bmbie-d2" % n,
+                                 "instances": n, "ns": [w.ns for w in ws], "nt": nts,
+                                 "instance_steps": tot, "setup_s": round(setup_s, 1),
+                                 "excluded": "Ns=20480 instances: the direct form needs 15 GB of coefficients "
+                                             "each, and FMM steps are not graph-replayed"},
                       "plain_launches": tot / t_plain, "graph_per_instance": tot / t_graph,
+                      "batch_equals_plain": bool(same), "gpu_launches_plain": int(launches),
                       "timing": "host clock around each mode, device synchronised"}))
 
 

@@ -179,8 +179,12 @@ int tdbem_step_graph(tdbem_ctx *ctx, int32_t nsteps);
  * graph in which every instance's step is an independent branch, so that
  * small instances share the GPU.  tdbem_batch_create captures the graph
  * (the contexts must outlive the batch and not be stepped otherwise while
- * it exists); tdbem_batch_step advances every instance nsteps steps
- * (asynchronous; ordered after and before each context's stream);
+ * it exists); tdbem_batch_step advances every instance nsteps steps, or
+ * to its last step Nt-1 if that comes first (instances may have different
+ * Nt: one at its end stops, its kernels in later replays test the
+ * device-side step counter and do nothing; stepping with every instance at
+ * its end is a no-op; asynchronous; ordered after and before each
+ * context's stream);
  * tdbem_batch_sync waits and reports the first device-side error.  Results
  * are identical to stepping each context alone. */
 typedef struct tdbem_batch tdbem_batch;
@@ -226,8 +230,10 @@ int tdbem_set_precond(tdbem_ctx *ctx, const tdbem_sai *sai, int32_t *use_sai, in
  * tdbem_checkpoint: buf = NULL sets *len to the size needed; otherwise buf
  * (host, *len bytes) receives the state (synchronises).  tdbem_restore
  * loads it into a context prepared for the same problem (same mesh, BC,
- * known data, incident wave and parameters; ERR_ARG otherwise); stepping
- * then continues exactly as the checkpointed context would. */
+ * known data, incident wave and parameters; ERR_ARG otherwise), which may
+ * be the checkpointed context itself at a later step (a rewind: the steps
+ * after the checkpoint return to their initial state); stepping then
+ * continues exactly as the checkpointed context would. */
 int tdbem_checkpoint(const tdbem_ctx *ctx, void *buf, size_t *len);
 int tdbem_restore(tdbem_ctx *ctx, const void *buf, size_t len);
 

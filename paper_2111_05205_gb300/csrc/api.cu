@@ -252,6 +252,28 @@ int tdbem_set_incident_plane(tdbem_ctx *c, const double dir[3], double t0, doubl
     return TDBEM_OK;
 }
 
+// Steps 0..Nt-1 of the histories back to their state before the first step:
+// the known data (collocated, Eq. linear) and zero unknown components, and
+// the float-pair copies of the split form.
+static int reset_histories(tdbem_ctx *c)
+{
+    const int nt = c->P.nt, ns = c->ns;
+    const size_t nh = (size_t)nt * ns;
+    TD_CUDA(cudaMemsetAsync(c->d_u, 0, nh * sizeof(double), c->s));
+    TD_CUDA(cudaMemsetAsync(c->d_q, 0, nh * sizeof(double), c->s));
+    if (!c->kbar.empty()) {
+        double *d_f = nullptr;
+        TD_CUDA(dalloc(c, &d_f, (size_t)(nt - 1) * ns));
+        TD_CUDA(cudaMemcpyAsync(d_f, c->kbar.data(), (size_t)(nt - 1) * ns * sizeof(double),
+                                cudaMemcpyHostToDevice, c->s));
+        TD_CUDA(launch_known_collocation(c, d_f));
+        TD_CUDA(cudaStreamSynchronize(c->s));
+        dfree(c, d_f);
+    }
+    if (c->split) TD_CUDA(launch_split_histories(c));
+    return TDBEM_OK;
+}
+
 int tdbem_prepare(tdbem_ctx *c)
 {
     if (!c) return TDBEM_ERR_ARG;
@@ -413,19 +435,10 @@ int tdbem_prepare(tdbem_ctx *c)
     const size_t npad = (size_t)c->gmax * ns;
     TD_CUDA(dalloc(c, &c->d_u, npad + nh));
     TD_CUDA(dalloc(c, &c->d_q, npad + nh));
-    TD_CUDA(cudaMemsetAsync(c->d_u, 0, (npad + nh) * sizeof(double), c->s));
-    TD_CUDA(cudaMemsetAsync(c->d_q, 0, (npad + nh) * sizeof(double), c->s));
+    TD_CUDA(cudaMemsetAsync(c->d_u, 0, npad * sizeof(double), c->s));
+    TD_CUDA(cudaMemsetAsync(c->d_q, 0, npad * sizeof(double), c->s));
     c->d_u += npad;
     c->d_q += npad;
-    if (has_k) {
-        double *d_f = nullptr;
-        TD_CUDA(dalloc(c, &d_f, (size_t)(nt - 1) * ns));
-        TD_CUDA(cudaMemcpyAsync(d_f, c->kbar.data(), (size_t)(nt - 1) * ns * sizeof(double),
-                                cudaMemcpyHostToDevice, c->s));
-        TD_CUDA(launch_known_collocation(c, d_f));
-        TD_CUDA(cudaStreamSynchronize(c->s));
-        dfree(c, d_f);
-    }
     if (c->split) {
         TD_CUDA(dalloc(c, &c->d_us, npad + nh));
         TD_CUDA(dalloc(c, &c->d_qs, npad + nh));
@@ -433,9 +446,10 @@ int tdbem_prepare(tdbem_ctx *c)
         TD_CUDA(cudaMemsetAsync(c->d_qs, 0, npad * sizeof(float2), c->s));
         c->d_us += npad;
         c->d_qs += npad;
-        TD_CUDA(launch_split_histories(c));
-        TD_CUDA(launch_split_coefficients(c));
     }
+    int rh = reset_histories(c);
+    if (rh != TDBEM_OK) return rh;
+    if (c->split) TD_CUDA(launch_split_coefficients(c));
     TD_CUDA(dalloc(c, &c->d_b, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xa, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xb, (size_t)ns));
@@ -882,6 +896,10 @@ int tdbem_restore(tdbem_ctx *c, const void *buf, size_t len)
         c->alpha = keep;
         return fail(c, TDBEM_ERR_ARG, "checkpoint truncated");
     }
+    // steps past the restore point go back to their initial state (known
+    // data only), so a context can also be rewound
+    int rh = reset_histories(c);
+    if (rh != TDBEM_OK) return rh;
     TD_CUDA(cudaStreamSynchronize(c->s));
     const char *o = (const char *)buf + sizeof(h);
     for (auto &p : parts) {
@@ -1005,12 +1023,13 @@ int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out)
 int tdbem_batch_step(tdbem_batch *B, int32_t nsteps)
 {
     if (!B || nsteps < 0) return TDBEM_ERR_ARG;
-    for (tdbem_ctx *c : B->ctx)
-        if (c->alpha + nsteps > c->P.nt - 1) {
-            B->err = "an instance would step past its Nt-1";
-            return TDBEM_ERR_ARG;
-        }
-    if (nsteps == 0) return TDBEM_OK;
+    // instances of uneven Nt: one that reaches its step Nt-1 stops there (its
+    // kernels test the device-side step counter and do nothing), the others
+    // go on; the replay count is the largest number of steps any has left
+    int left = 0;
+    for (tdbem_ctx *c : B->ctx) left = std::max(left, std::min(nsteps, c->P.nt - 1 - c->alpha));
+    if (left == 0) return TDBEM_OK;
+    nsteps = left;
     for (tdbem_ctx *c : B->ctx) {
         cudaError_t e = join(c->user, B->s);
         int a = c->alpha + 1;
@@ -1028,8 +1047,9 @@ int tdbem_batch_step(tdbem_batch *B, int32_t nsteps)
         }
     }
     for (tdbem_ctx *c : B->ctx) {
-        c->alpha += nsteps;
-        c->steps_total += nsteps;
+        const int done = std::min(nsteps, c->P.nt - 1 - c->alpha);
+        c->alpha += done;
+        c->steps_total += done;
         c->launches[PH_NEAR] += nsteps;
         c->launches[PH_SOLVE] += (int64_t)nsteps * c->solve_iters;
         cudaError_t e = join(B->s, c->user);

@@ -181,31 +181,54 @@ namespace tdbem {
 // P2M at the leaf level for source interval k (Section 3, moment M_{b,n}):
 // M[c][b + P3 n] += pref sum_{sigma in J_k} sum_{j in c}
 //                   (At[j][b] tau_j^sigma - As[j][b] sigma_j^sigma) ell_n(t_sigma),
-// with tau, sigma the folded histories of Eq. tau / Eq. sigma.
+// with tau, sigma the folded histories of Eq. tau / Eq. sigma.  The sum over
+// sigma does not involve the spatial node b, so it is taken first, once per
+// (element, temporal node): Tq[j][n] = sum_sigma tau_j^sigma ell_n(t_sigma)
+// (Tu likewise with sigma_j), staged in shared memory for kP2MChunk
+// elements at a time; then M[b + P3 n] += pref sum_j (At Tq - As Tu).
+constexpr int kP2MChunk = 32;
+
 __global__ void k_p2m(int P3, int P, int Lt, int k, int d, int ns, int smax_hist, const int32_t *__restrict__ cstart,
                       const int32_t *__restrict__ perm, const double *__restrict__ At, const double *__restrict__ As,
                       const double *__restrict__ q, const double *__restrict__ u, const double *__restrict__ wk,
                       const double *__restrict__ tl, double pref, double *M)
 {
-    int c = blockIdx.x;
-    for (int e = threadIdx.x; e < P; e += blockDim.x) {
-        int b = e % P3, n = e / P3;
-        double acc = 0.0;
-        for (int pos = cstart[c]; pos < cstart[c + 1]; ++pos) {
-            int j = perm[pos];
-            double at = At[(int64_t)j * P3 + b], as = As[(int64_t)j * P3 + b];
+    __shared__ double Tq[kP2MChunk][8], Tu[kP2MChunk][8];
+    __shared__ int jj[kP2MChunk];
+    const int c = blockIdx.x, pt = P / P3;
+    const int e0 = cstart[c], e1 = cstart[c + 1];
+    for (int base = e0; base < e1; base += kP2MChunk) {
+        const int nj = min(kP2MChunk, e1 - base);
+        for (int x = threadIdx.x; x < nj * pt; x += blockDim.x) {
+            const int jl = x / pt, n = x % pt;
+            const int j = perm[base + jl];
+            double tq = 0.0, tu = 0.0;
             for (int t = 0; t < Lt; ++t) {
-                int sg = k * Lt + t;
+                const int sg = k * Lt + t;
                 if (sg > smax_hist) break;
                 double tau = 0.0, sig = 0.0;
                 for (int kk = 0; kk <= d + 1 && kk <= sg; ++kk) {
                     tau += wk[kk] * q[(int64_t)(sg - kk) * ns + j];
                     sig += wk[kk] * u[(int64_t)(sg - kk) * ns + j];
                 }
-                acc += (at * tau - as * sig) * tl[t * 8 + n];
+                tq += tau * tl[t * 8 + n];
+                tu += sig * tl[t * 8 + n];
             }
+            Tq[jl][n] = tq;
+            Tu[jl][n] = tu;
+            if (n == 0) jj[jl] = j;
         }
-        M[(int64_t)c * P + e] += pref * acc;
+        __syncthreads();
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            const int b = e % P3, n = e / P3;
+            double acc = 0.0;
+            for (int jl = 0; jl < nj; ++jl) {
+                const int64_t r = (int64_t)jj[jl] * P3 + b;
+                acc += At[r] * Tq[jl][n] - As[r] * Tu[jl][n];
+            }
+            M[(int64_t)c * P + e] += pref * acc;
+        }
+        __syncthreads();
     }
 }
 
@@ -378,25 +401,45 @@ __global__ void k_m2l_recurrence(int64_t n, int d, int mu, int nslot, int k, con
 // L2P (Eq. target_m2l) at the leaf level for the Lt steps of observation
 // interval I_k: far[t][i] = sum_{a,m} D_a(x_i) ell_m(t_alpha) L_{a,m}, with
 // the Burton-Miller operator (d/dn_x - c^-1 d/dt) applied to ell_a ell_m.
+// The spatial sum is taken first, once per temporal node:
+// Yn[m] = sum_a (n.grad ell_a)(x_i) L_{a,m}, Yv[m] = sum_a ell_a(x_i) L_{a,m};
+// then far[t] = sum_m (ell_m(t) Yn[m] - ell_m'(t) Yv[m] / c) (BMBIE) or
+// sum_m ell_m(t) Yv[m] (OBIE).  One warp per element: the lanes read the
+// element's basis rows and the cell's locals contiguously and the sums are
+// reduced by shuffles.
 __global__ void k_l2p(int ns, int P3, int pt, int Lt, int bie, double c, const int32_t *__restrict__ e2c,
                       const double *__restrict__ Lloc, const double *__restrict__ Dv, const double *__restrict__ Dn,
                       const double *__restrict__ tl, const double *__restrict__ dtl, double *far)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (i >= ns) return;  // whole warps leave together
     const double *L = Lloc + (int64_t)e2c[i] * P3 * pt;
-    for (int t = 0; t < Lt; ++t) {
-        double s = 0.0;
-        for (int m = 0; m < pt; ++m) {
-            double lm = tl[t * 8 + m], dlm = dtl[t * 8 + m];
-            for (int a = 0; a < P3; ++a) {
-                double Lam = L[a + P3 * m];
-                if (bie)
-                    s += (Dn[(int64_t)i * P3 + a] * lm - Dv[(int64_t)i * P3 + a] * dlm / c) * Lam;
-                else
-                    s += Dv[(int64_t)i * P3 + a] * lm * Lam;
+    const double *dv = Dv + (int64_t)i * P3, *dn = Dn + (int64_t)i * P3;
+    double yv[8], yn[8];
+    for (int m = 0; m < 8; ++m) yv[m] = yn[m] = 0.0;
+    for (int a = lane; a < P3; a += 32) {
+        const double v = dv[a], w = bie ? dn[a] : 0.0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (m < pt) {
+                const double Lam = L[a + P3 * m];
+                yv[m] += v * Lam;
+                yn[m] += w * Lam;
             }
-        }
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        if (m < pt)
+            for (int o = 16; o; o >>= 1) {
+                yv[m] += __shfl_xor_sync(0xffffffffu, yv[m], o);
+                yn[m] += __shfl_xor_sync(0xffffffffu, yn[m], o);
+            }
+    for (int t = lane; t < Lt; t += 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (m < pt) s += bie ? (tl[t * 8 + m] * yn[m] - dtl[t * 8 + m] * yv[m] / c) : tl[t * 8 + m] * yv[m];
         far[(int64_t)t * ns + i] = s;
     }
 }
@@ -431,16 +474,47 @@ template <typename TC>
 __global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
                              const int64_t *__restrict__ oidx, const TC *__restrict__ C, double *ring, double *G)
 {
+    // R = nblk P entries per column, a multiple of 4 (P = ps^3 pt with ps even
+    // or pt even is not guaranteed, so the vector path checks); each thread
+    // sums 4 consecutive entries over the cell's pairs, 4 pairs at a time
     const int R = nblk * P;
-    int O = blockIdx.x;
-    for (int e = threadIdx.x; e < R; e += blockDim.x) {
-        double s = 0.0;
-        for (int64_t t = ooff[O]; t < ooff[O + 1]; ++t) s += (double)C[(int64_t)oidx[t] * R + e];
-        int blk = e / P, r = e % P;
-        if (blk <= mu)
-            ring[((int64_t)((k + blk + 1) % nslot) * nc + O) * P + r] += s;
-        else
-            G[((int64_t)(blk - mu - 1) * nc + O) * P + r] = s;
+    const int O = blockIdx.x;
+    const int64_t t0 = ooff[O], t1 = ooff[O + 1];
+    for (int e0 = 4 * threadIdx.x; e0 < R; e0 += 4 * blockDim.x) {
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        if ((R & 3) == 0) {
+            int64_t t = t0;
+            for (; t + 4 <= t1; t += 4) {
+                double a[4][4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const TC *src = C + oidx[t + v] * R + e0;
+                    if constexpr (sizeof(TC) == 4) {
+                        const float4 f = *reinterpret_cast<const float4 *>(src);
+                        a[v][0] = f.x, a[v][1] = f.y, a[v][2] = f.z, a[v][3] = f.w;
+                    } else {
+                        for (int q = 0; q < 4; ++q) a[v][q] = src[q];
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    for (int q = 0; q < 4; ++q) s[q] += a[v][q];
+            }
+            for (; t < t1; ++t) {
+                const TC *src = C + oidx[t] * R + e0;
+                for (int q = 0; q < 4; ++q) s[q] += (double)src[q];
+            }
+        } else {
+            for (int q = 0; q < 4 && e0 + q < R; ++q)
+                for (int64_t t = t0; t < t1; ++t) s[q] += (double)C[oidx[t] * R + e0 + q];
+        }
+        for (int q = 0; q < 4 && e0 + q < R; ++q) {
+            const int e = e0 + q, blk = e / P, r = e % P;
+            if (blk <= mu)
+                ring[((int64_t)((k + blk + 1) % nslot) * nc + O) * P + r] += s[q];
+            else
+                G[((int64_t)(blk - mu - 1) * nc + O) * P + r] = s[q];
+        }
     }
 }
 
@@ -689,7 +763,13 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     if (cublasCreate(&F.blas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     cublasSetStream(F.blas, c->s);
     cublasSetMathMode(F.blas, CUBLAS_DEFAULT_MATH);
-    if (c->split) cublasSetEmulationStrategy(F.blas, CUBLAS_EMULATION_STRATEGY_EAGER);
+    if (c->split) {
+        cublasSetEmulationStrategy(F.blas, CUBLAS_EMULATION_STRATEGY_EAGER);
+        // moments and operators are finite: the unknowns are checked every
+        // step (a non-finite value stops the march), so the emulation need
+        // not scan its operands for infinities and NaNs
+        cublasSetEmulationSpecialValuesSupport(F.blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
+    }
 
     // per-element tables (leaf boxes)
     F_TRY(falloc(c, &F.At, (size_t)ns * P3));
@@ -938,7 +1018,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
     }
     // L2P for observation interval k + 1
     FmmLevel &V = F.lev[L];
-    k_l2p<<<(c->ns + 127) / 128, 128, 0, s>>>(c->ns, F.P3, F.pt, F.Lt, c->P.bie, c->P.c, c->tree.e2c,
+    k_l2p<<<(int)(((int64_t)c->ns * 32 + 127) / 128), 128, 0, s>>>(c->ns, F.P3, F.pt, F.Lt, c->P.bie, c->P.c, c->tree.e2c,
                                               V.ring + (size_t)((k + 1) % F.nslot) * V.nc * P, F.Dv, F.Dn, F.tl,
                                               F.dtl, F.far);
     return cudaGetLastError();

@@ -5,7 +5,6 @@
 namespace tdbem {
 
 constexpr int kNearThreads = 128;
-constexpr int kUnroll = 8;  // full window slots whose loads are issued together
 constexpr int kMaxFull = 6;       // full window slots handled by the unrolled bodies
 constexpr int kNearPrefetch = 2;  // blocks of a warp whose coefficients are asked of L2 ahead
 
@@ -170,7 +169,7 @@ __device__ __forceinline__ void near_slots_rest(const typename NearV<SPLIT>::T *
     }
 }
 
-template <bool HU, bool HW, bool SPLIT>
+template <bool HU, bool HW, bool SPLIT, int MAXF>
 __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__restrict__ kub,
                                            const typename NearV<SPLIT>::T *__restrict__ kwb,
                                            const typename NearV<SPLIT>::T *__restrict__ hqb,
@@ -181,7 +180,7 @@ __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__res
     const int cmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
     const bool tail = cmax > cmin;
     // both kinds at once keep twice the values per slot in registers
-    constexpr int MF = (HU && HW) ? kMaxFull / 2 : kMaxFull;
+    constexpr int MF = (HU && HW) ? MAXF / 2 : MAXF;
     const int nf = cmin < MF ? cmin : MF;
 #define TDBEM_NEAR_CASE(n)                                                                                     \
     case n:                                                                                                    \
@@ -204,7 +203,9 @@ __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__res
 }
 
 // Asks L2 to fetch the coefficient bytes [a, e) of a block ahead of its
-// use, so the warp's own loads wait for an L2 hit rather than HBM.
+// use, so the warp's own loads wait for an L2 hit rather than HBM: lane l
+// names the l-th 128-byte line of the range (a block spans at most 31).
+// (One bulk prefetch per block through the copy engine measured slower.)
 __device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_t e, int lane)
 {
     const size_t end = __cvta_generic_to_global(k + e);
@@ -212,7 +213,7 @@ __device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_
     if (p < end) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-template <bool HU, bool HW, bool SPLIT>
+template <bool HU, bool HW, bool SPLIT, int MAXF>
 __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t *__restrict__ prow,
                                          const int32_t *__restrict__ col, const int64_t *__restrict__ rowblk,
                                          const uint16_t *__restrict__ meta, const int64_t *__restrict__ boff,
@@ -282,7 +283,7 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
         // beta = alpha - g0 - s
         const int g0 = (int)(m & kMaxG0), cnt = (int)(m >> kG0Bits);
         const int64_t hb = (int64_t)(alpha - g0) * ns + j;
-        near_block<HU, HW, SPLIT>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
+        near_block<HU, HW, SPLIT, MAXF>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
         if (SPLIT) df_renorm(dacc);
     }
 }
@@ -295,8 +296,8 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
 // SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
 // coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
 // are read from their float-pair copies and the sum runs in double-float.
-template <bool HU, bool HW, bool SPLIT>
-__global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
+template <bool HU, bool HW, bool SPLIT, int MINB, int MAXF>
+__global__ void __launch_bounds__(kNearThreads, MINB) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
                                                               const int64_t *__restrict__ prow,
                                                               const int32_t *__restrict__ col,
                                                               const int64_t *__restrict__ rowblk,
@@ -311,15 +312,20 @@ __global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha,
                                                               const double *__restrict__ exc, Incident inc,
                                                               const double *__restrict__ xc,
                                                               const double *__restrict__ nrm,
-                                                              const double *__restrict__ far, double *b)
+                                                              const double *__restrict__ far, int alim, double *b)
 {
     __shared__ double red[kNearThreads / 32];
-    if (alpha_dev) alpha = *alpha_dev;
+    if (alpha_dev) {
+        // graph-replayed steps: an instance past its last step (alim = Nt-1)
+        // does nothing while the others of its batch go on (whole CTA)
+        alpha = *alpha_dev;
+        if (alpha > alim) return;
+    }
     const int i = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double acc = 0.0;
     DF dacc = {0.f, 0.f};
-    near_row<HU, HW, SPLIT>(i, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
+    near_row<HU, HW, SPLIT, MAXF>(i, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
     if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
@@ -337,21 +343,33 @@ __global__ void __launch_bounds__(kNearThreads, 8) k_near_sum(int ns, int alpha,
     }
 }
 
-template <bool SPLIT>
+template <bool SPLIT, int MINB, int MAXF>
 static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
     bool hu = c->d_ku != nullptr, hw = c->d_kw != nullptr;
-    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT> : k_near_sum<true, false, SPLIT>)
-                : (hw ? k_near_sum<false, true, SPLIT> : k_near_sum<false, false, SPLIT>);
+    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, MINB, MAXF> : k_near_sum<true, false, SPLIT, MINB, MAXF>)
+                : (hw ? k_near_sum<false, true, SPLIT, MINB, MAXF> : k_near_sum<false, false, SPLIT, MINB, MAXF>);
     k<<<c->ns, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
-                                       c->d_n, d_far, c->d_b);
+                                       c->d_n, d_far, c->P.nt - 1, c->d_b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
-    return c->split ? near_dispatch<true>(c, alpha, d_exc, d_far) : near_dispatch<false>(c, alpha, d_exc, d_far);
+    static int occ = -1;
+    if (occ < 0) {
+        const char *v = getenv("TDBEM_NEAR_OCC");
+        occ = v ? atoi(v) : 0;
+    }
+    if (occ == 1)
+        return c->split ? near_dispatch<true, 9, 5>(c, alpha, d_exc, d_far)
+                        : near_dispatch<false, 9, 5>(c, alpha, d_exc, d_far);
+    if (occ == 2)
+        return c->split ? near_dispatch<true, 10, 4>(c, alpha, d_exc, d_far)
+                        : near_dispatch<false, 10, 4>(c, alpha, d_exc, d_far);
+    return c->split ? near_dispatch<true, 8, kMaxFull>(c, alpha, d_exc, d_far)
+                    : near_dispatch<false, 8, kMaxFull>(c, alpha, d_exc, d_far);
 }
 
 __device__ __forceinline__ float2 split2(double v)
@@ -399,11 +417,15 @@ __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, con
                          const double *__restrict__ ainv, const double *__restrict__ b,
                          const double *__restrict__ xin, double *xout, int last, int64_t row,
                          const int *__restrict__ alpha_dev, const int8_t *__restrict__ phi, double *u, double *q,
-                         float2 *us, float2 *qs, int *flag)
+                         float2 *us, float2 *qs, int alim, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
-    if (alpha_dev) row = (int64_t)(*alpha_dev - 1) * ns;
+    if (alpha_dev) {
+        const int a = *alpha_dev;
+        if (a > alim) return;  // instance past its last step
+        row = (int64_t)(a - 1) * ns;
+    }
     double s = b[i];
     if (xin) {
         for (int k = 0; k < width; ++k) {
@@ -430,16 +452,20 @@ cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last)
     int64_t row = (int64_t)(alpha - 1) * c->ns;
     k_jacobi<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->ell_w, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, xout, last,
                                                    row, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_phi, c->d_u,
-                                                   c->d_q, c->d_us, c->d_qs, c->d_flag);
+                                                   c->d_q, c->d_us, c->d_qs, c->P.nt - 1, c->d_flag);
     return cudaGetLastError();
 }
 
-// Advances the device-side step counter (graph-replayed steps).
-__global__ void k_alpha_next(int *alpha_dev) { *alpha_dev += 1; }
+// Advances the device-side step counter (graph-replayed steps), stopping
+// one past the last step alim = Nt-1.
+__global__ void k_alpha_next(int *alpha_dev, int alim)
+{
+    if (*alpha_dev <= alim) *alpha_dev += 1;
+}
 
 cudaError_t launch_alpha_next(tdbem_ctx *c)
 {
-    k_alpha_next<<<1, 1, 0, c->s>>>(c->d_alpha);
+    k_alpha_next<<<1, 1, 0, c->s>>>(c->d_alpha, c->P.nt - 1);
     return cudaGetLastError();
 }
 

@@ -70,8 +70,8 @@ def test_batch_equals_each_instance_alone():
             abi.tdbem_batch_step(B, 10)
             abi.tdbem_batch_step(B, nsteps - 10)
             abi.tdbem_batch_sync(B)
-            with pytest.raises(abi.TdbemError):
-                abi.tdbem_batch_step(B, 1)  # past Nt-1
+            abi.tdbem_batch_step(B, 5)  # every instance at Nt-1: nothing happens
+            abi.tdbem_batch_sync(B)
         finally:
             abi.tdbem_batch_destroy(B)
         for s, w, r in zip(sols, ws, ref):
@@ -98,3 +98,39 @@ def test_batch_rejects_fmm_and_duplicates():
     finally:
         f.close()
         d.close()
+
+
+def test_batch_of_uneven_nt():
+    """Instances of different Nt in one batch: each stops at its own step
+    Nt-1 (its kernels see the device-side step counter past the end and do
+    nothing) while the others go on, and every history equals the instance
+    stepped alone to its end."""
+    _need_gpu()
+    from paper_2111_05205_gb300 import abi
+    spec = [("ellipsoid80_bmbie_d2_hard_plane_s7", 0, 12), ("ellipsoid320_obie_d1_hard_plane_s3", 1, 30),
+            ("sphere80_bmbie_d1_dirichlet_uniform", 1, 21), ("ellipsoid80_bmbie_d2_hard_plane_s9", 1, 40)]
+    ws = [case(n, nt=nt) for n, _, nt in spec]
+    ref = []
+    for w, (n, prec, nt) in zip(ws, spec):
+        s = gpu_solver(w, precision=prec)
+        try:
+            abi.tdbem_step(s.ctx, nt - 1)
+            ref.append(_unknown(s, w, nt - 1))
+        finally:
+            s.close()
+    sols = [gpu_solver(w, precision=prec) for w, (n, prec, nt) in zip(ws, spec)]
+    try:
+        B = abi.tdbem_batch_create([s.ctx for s in sols])
+        try:
+            abi.tdbem_batch_step(B, 7)
+            abi.tdbem_batch_step(B, 25)  # the first instance stops at 11, the third at 20
+            abi.tdbem_batch_step(B, 100)  # the last goes to 39
+            abi.tdbem_batch_sync(B)
+        finally:
+            abi.tdbem_batch_destroy(B)
+        for s, w, r, (n, prec, nt) in zip(sols, ws, ref, spec):
+            assert abi.tdbem_steps_done(s.ctx) == nt - 1
+            assert np.array_equal(_unknown(s, w, nt - 1), r)
+    finally:
+        for s in sols:
+            s.close()

@@ -1,7 +1,8 @@
 """Checkpoint at a step, restore into a fresh context, continue: the result
 equals the uninterrupted run bit for bit (deterministic kernels), for the
 direct path and the FMM path, including a restore point inside a leaf
-interval of the FMM."""
+interval of the FMM.  Restoring the finished context itself (a rewind) and
+marching again gives the same result too."""
 
 import numpy as np
 import pytest
@@ -32,6 +33,12 @@ def test_checkpoint_resume_is_exact(kind, k):
         ua, _ = a.solution()
         ub, _ = b.solution()
         assert np.array_equal(ua, ub)
+        # rewind the finished context to the checkpoint and march again
+        abi.tdbem_restore(a.ctx, blob)
+        assert abi.tdbem_steps_done(a.ctx) == k
+        abi.tdbem_step(a.ctx, 35 - k)
+        ur, _ = a.solution()
+        assert np.array_equal(ur, ua)
         with pytest.raises(abi.TdbemError):
             abi.tdbem_restore(b.ctx, blob[:40])
     finally:
