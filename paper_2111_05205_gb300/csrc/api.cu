@@ -360,6 +360,9 @@ int tdbem_prepare(tdbem_ctx *c)
     if (mx[1] > kMaxG0) return fail(c, TDBEM_ERR_ARG, "lag beyond 4095 (surface too large for c*dt)");
     c->smax = std::max(mx[0], 1);
     c->gmax = mx[2];
+    // short rows (fewer than 8 blocks on average) get one warp per row; long
+    // ones (all pairs) four warps sharing a row's blocks
+    c->near_wpr = (c->nbt < (int64_t)8 * ns) ? 1 : 4;
 
     // packed coefficient layout: block offsets by a prefix on the host
     {

@@ -474,39 +474,44 @@ template <typename TC>
 __global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
                              const int64_t *__restrict__ oidx, const TC *__restrict__ C, double *ring, double *G)
 {
-    // R = nblk P entries per column, a multiple of 4 (P = ps^3 pt with ps even
-    // or pt even is not guaranteed, so the vector path checks); each thread
-    // sums 4 consecutive entries over the cell's pairs, 4 pairs at a time
+    // The cell's column indices are staged in shared memory (an interaction
+    // list holds at most 189 cells), so the operand loads do not wait on
+    // index loads.  Each thread sums 4 consecutive entries (one 16-byte load
+    // per column when R = nblk P is a multiple of 4) over the cell's columns
+    // in list order, 8 columns' loads at a time.
+    __shared__ int64_t cols[kMaxIL];
     const int R = nblk * P;
     const int O = blockIdx.x;
-    const int64_t t0 = ooff[O], t1 = ooff[O + 1];
+    const int64_t t0 = ooff[O];
+    const int nt = (int)(ooff[O + 1] - t0);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) cols[t] = oidx[t0 + t] * R;
+    __syncthreads();
     for (int e0 = 4 * threadIdx.x; e0 < R; e0 += 4 * blockDim.x) {
         double s[4] = {0.0, 0.0, 0.0, 0.0};
-        if ((R & 3) == 0) {
-            int64_t t = t0;
-            for (; t + 4 <= t1; t += 4) {
-                double a[4][4];
+        if ((R & 3) == 0 && sizeof(TC) == 4) {
+            int t = 0;
+            for (; t + 8 <= nt; t += 8) {
+                float4 f[8];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const TC *src = C + oidx[t + v] * R + e0;
-                    if constexpr (sizeof(TC) == 4) {
-                        const float4 f = *reinterpret_cast<const float4 *>(src);
-                        a[v][0] = f.x, a[v][1] = f.y, a[v][2] = f.z, a[v][3] = f.w;
-                    } else {
-                        for (int q = 0; q < 4; ++q) a[v][q] = src[q];
-                    }
+                for (int v = 0; v < 8; ++v) f[v] = *reinterpret_cast<const float4 *>(C + cols[t + v] + e0);
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    s[0] += f[v].x;
+                    s[1] += f[v].y;
+                    s[2] += f[v].z;
+                    s[3] += f[v].w;
                 }
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    for (int q = 0; q < 4; ++q) s[q] += a[v][q];
             }
-            for (; t < t1; ++t) {
-                const TC *src = C + oidx[t] * R + e0;
-                for (int q = 0; q < 4; ++q) s[q] += (double)src[q];
+            for (; t < nt; ++t) {
+                const float4 f = *reinterpret_cast<const float4 *>(C + cols[t] + e0);
+                s[0] += f.x;
+                s[1] += f.y;
+                s[2] += f.z;
+                s[3] += f.w;
             }
         } else {
             for (int q = 0; q < 4 && e0 + q < R; ++q)
-                for (int64_t t = t0; t < t1; ++t) s[q] += (double)C[oidx[t] * R + e0 + q];
+                for (int t = 0; t < nt; ++t) s[q] += (double)C[cols[t] + e0 + q];
         }
         for (int q = 0; q < 4 && e0 + q < R; ++q) {
             const int e = e0 + q, blk = e / P, r = e % P;
@@ -688,7 +693,10 @@ static cudaError_t m2l_tune_and_finalize(tdbem_ctx *c, FmmLevel &V)
         for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = V.colbase[o] + (t - V.ostart[o]);
     std::vector<int64_t> ooff(V.nc + 1, 0);
     for (int32_t O : V.hpO) ooff[O + 1]++;
-    for (int O = 0; O < V.nc; ++O) ooff[O + 1] += ooff[O];
+    for (int O = 0; O < V.nc; ++O) {
+        if (ooff[O + 1] > kMaxIL) return cudaErrorInvalidValue;  // the reduction stages one list in shared memory
+        ooff[O + 1] += ooff[O];
+    }
     std::vector<int64_t> oidx(V.np), fill(ooff.begin(), ooff.end() - 1);
     for (int64_t t = 0; t < V.np; ++t) oidx[fill[V.hpO[t]]++] = pcol[t];
     cudaError_t e;

@@ -5,7 +5,9 @@
 namespace tdbem {
 
 constexpr int kNearThreads = 128;
-constexpr int kMaxFull = 6;       // full window slots handled by the unrolled bodies
+constexpr int kNearWarps = kNearThreads / 32;
+constexpr int kNearMinBlocks = 10;  // split form: 48 registers, 40 resident warps per SM (measured best)
+constexpr int kMaxFull = 4;         // full window slots handled by the unrolled bodies
 constexpr int kNearPrefetch = 2;  // blocks of a warp whose coefficients are asked of L2 ahead
 
 // Incident-wave term e_i(t_a) of the total-field equation: u_in (OBIE) or
@@ -169,7 +171,7 @@ __device__ __forceinline__ void near_slots_rest(const typename NearV<SPLIT>::T *
     }
 }
 
-template <bool HU, bool HW, bool SPLIT, int MAXF>
+template <bool HU, bool HW, bool SPLIT>
 __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__restrict__ kub,
                                            const typename NearV<SPLIT>::T *__restrict__ kwb,
                                            const typename NearV<SPLIT>::T *__restrict__ hqb,
@@ -180,7 +182,7 @@ __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__res
     const int cmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
     const bool tail = cmax > cmin;
     // both kinds at once keep twice the values per slot in registers
-    constexpr int MF = (HU && HW) ? MAXF / 2 : MAXF;
+    constexpr int MF = (HU && HW) ? kMaxFull / 2 : kMaxFull;
     const int nf = cmin < MF ? cmin : MF;
 #define TDBEM_NEAR_CASE(n)                                                                                     \
     case n:                                                                                                    \
@@ -213,8 +215,8 @@ __device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_
     if (p < end) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-template <bool HU, bool HW, bool SPLIT, int MAXF>
-__device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t *__restrict__ prow,
+template <bool HU, bool HW, bool SPLIT, int WPR>
+__device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const int64_t *__restrict__ prow,
                                          const int32_t *__restrict__ col, const int64_t *__restrict__ rowblk,
                                          const uint16_t *__restrict__ meta, const int64_t *__restrict__ boff,
                                          const double *__restrict__ ku, const double *__restrict__ kw,
@@ -223,7 +225,7 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
                                          double &acc)
 {
     using V = typename NearV<SPLIT>::T;
-    constexpr int W = kNearThreads / 32;
+    constexpr int W = WPR;  // the row's warps take its blocks in turn
     const V *hq, *hu;
     if constexpr (SPLIT) {
         hq = qs;
@@ -232,7 +234,7 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
         hq = q;
         hu = u_;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t p0 = prow[i];
     const int npr = (int)(prow[i + 1] - p0);
@@ -245,7 +247,7 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
     // the warp asks L2 for the coefficients of its block kNearPrefetch blocks
     // ahead (here: of its first kNearPrefetch blocks)
     for (int t = 0; t < kNearPrefetch; ++t) {
-        const int pb = warp + W * t;
+        const int pb = wr + W * t;
         if (pb < nblk) {
             if (HU) near_prefetch(ku, orow[pb], orow[pb + 1], lane);
             if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
@@ -253,7 +255,7 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
     }
     // metadata of the first block; the next block's is fetched while the
     // current one is summed
-    int bk = warp;
+    int bk = wr;
     unsigned mnext = 0u;
     int64_t onext = 0;
     if (bk < nblk) {
@@ -283,7 +285,7 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
         // beta = alpha - g0 - s
         const int g0 = (int)(m & kMaxG0), cnt = (int)(m >> kG0Bits);
         const int64_t hb = (int64_t)(alpha - g0) * ns + j;
-        near_block<HU, HW, SPLIT, MAXF>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
+        near_block<HU, HW, SPLIT>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
         if (SPLIT) df_renorm(dacc);
     }
 }
@@ -296,8 +298,8 @@ __device__ __forceinline__ void near_row(int i, int ns, int alpha, const int64_t
 // SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
 // coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
 // are read from their float-pair copies and the sum runs in double-float.
-template <bool HU, bool HW, bool SPLIT, int MINB, int MAXF>
-__global__ void __launch_bounds__(kNearThreads, MINB) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
+template <bool HU, bool HW, bool SPLIT, int WPR>
+__global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
                                                               const int64_t *__restrict__ prow,
                                                               const int32_t *__restrict__ col,
                                                               const int64_t *__restrict__ rowblk,
@@ -314,25 +316,26 @@ __global__ void __launch_bounds__(kNearThreads, MINB) k_near_sum(int ns, int alp
                                                               const double *__restrict__ nrm,
                                                               const double *__restrict__ far, int alim, double *b)
 {
-    __shared__ double red[kNearThreads / 32];
+    __shared__ double red[kNearWarps];
     if (alpha_dev) {
         // graph-replayed steps: an instance past its last step (alim = Nt-1)
         // does nothing while the others of its batch go on (whole CTA)
         alpha = *alpha_dev;
         if (alpha > alim) return;
     }
-    const int i = blockIdx.x;
+    // WPR warps per row, kNearWarps / WPR rows per CTA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kNearWarps / WPR) + warp / WPR, wr = warp % WPR;
     double acc = 0.0;
     DF dacc = {0.f, 0.f};
-    near_row<HU, HW, SPLIT, MAXF>(i, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
+    if (i < ns) near_row<HU, HW, SPLIT, WPR>(i, wr, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
     if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lane == 0 && wr == 0 && i < ns) {
         double t = 0.0;
-        for (int w = 0; w < kNearThreads / 32; ++w) t += red[w];
+        for (int w = 0; w < WPR; ++w) t += red[warp + w];
         double e = 0.0;
         if (exc)
             e = exc[i];
@@ -343,13 +346,14 @@ __global__ void __launch_bounds__(kNearThreads, MINB) k_near_sum(int ns, int alp
     }
 }
 
-template <bool SPLIT, int MINB, int MAXF>
+template <bool SPLIT, int WPR>
 static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
     bool hu = c->d_ku != nullptr, hw = c->d_kw != nullptr;
-    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, MINB, MAXF> : k_near_sum<true, false, SPLIT, MINB, MAXF>)
-                : (hw ? k_near_sum<false, true, SPLIT, MINB, MAXF> : k_near_sum<false, false, SPLIT, MINB, MAXF>);
-    k<<<c->ns, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
+    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, WPR> : k_near_sum<true, false, SPLIT, WPR>)
+                : (hw ? k_near_sum<false, true, SPLIT, WPR> : k_near_sum<false, false, SPLIT, WPR>);
+    constexpr int rows = kNearWarps / WPR;
+    k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
                                        c->d_n, d_far, c->P.nt - 1, c->d_b);
     return cudaGetLastError();
@@ -357,19 +361,10 @@ static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, c
 
 cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
-    static int occ = -1;
-    if (occ < 0) {
-        const char *v = getenv("TDBEM_NEAR_OCC");
-        occ = v ? atoi(v) : 0;
-    }
-    if (occ == 1)
-        return c->split ? near_dispatch<true, 9, 5>(c, alpha, d_exc, d_far)
-                        : near_dispatch<false, 9, 5>(c, alpha, d_exc, d_far);
-    if (occ == 2)
-        return c->split ? near_dispatch<true, 10, 4>(c, alpha, d_exc, d_far)
-                        : near_dispatch<false, 10, 4>(c, alpha, d_exc, d_far);
-    return c->split ? near_dispatch<true, 8, kMaxFull>(c, alpha, d_exc, d_far)
-                    : near_dispatch<false, 8, kMaxFull>(c, alpha, d_exc, d_far);
+    if (c->near_wpr == 1)
+        return c->split ? near_dispatch<true, 1>(c, alpha, d_exc, d_far) : near_dispatch<false, 1>(c, alpha, d_exc, d_far);
+    return c->split ? near_dispatch<true, kNearWarps>(c, alpha, d_exc, d_far)
+                    : near_dispatch<false, kNearWarps>(c, alpha, d_exc, d_far);
 }
 
 __device__ __forceinline__ float2 split2(double v)

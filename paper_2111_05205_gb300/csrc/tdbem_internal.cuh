@@ -15,6 +15,7 @@ namespace tdbem {
 // Pair metadata: lag window start g0 (12 bits) and length cnt (4 bits).
 constexpr int kG0Bits = 12;
 constexpr int kMaxG0 = (1 << kG0Bits) - 1;
+constexpr int kMaxIL = 189;  // cells in one interaction list: 7^3 - 3^3 offsets, at most 189 occupied
 constexpr int kMaxCnt = 15;
 
 // Coefficient kinds (bit positions in a kinds mask).
@@ -157,6 +158,7 @@ struct tdbem_ctx {
     int64_t *d_boff = nullptr;   // [nbt+1] first coefficient of each block (last: ncoef)
     int smax = 0;                // largest window length
     int gmax = 0;                // largest lag stored
+    int near_wpr = 4;            // history sum: warps per row (1 for short rows)
     int64_t npairs = 0, ncoef = 0;
     int ku_kind = -1, kw_kind = -1;
     double *d_ku = nullptr, *d_kw = nullptr;
