@@ -418,11 +418,20 @@ def fp64_form(args, w, phi, stream):
 
 
 def _kernel_rev():
+    """Source revision of the history-sum kernel: a hash of its part of
+    csrc/march.cu (the file up to the end of its launcher: constants,
+    incident term, double-float helpers, kernel) and of
+    csrc/tdbem_internal.cuh."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("march.cu", "tdbem_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", "march.cu")) as fh:
+        src = fh.read()
+    a = 0
+    b = src.index("cudaError_t launch_near_sum(")
+    b = src.index("\n}\n", b)
+    h.update(src[a:b].encode())
+    with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", "tdbem_internal.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:12]
 
 

@@ -194,6 +194,18 @@ int tdbem_batch_sync(tdbem_batch *batch);
 void tdbem_batch_destroy(tdbem_batch *batch);
 const char *tdbem_batch_last_error(const tdbem_batch *batch);
 
+/* Self-check of the bounded grid barrier used by the fused zero-lag solve
+ * (plain stepping runs the solve's K Jacobi sweeps in one cooperative
+ * launch with a grid barrier between sweeps; every wait in it gives up
+ * after a bounded number of polls, about 0.3 s, and the step then reports
+ * TDBEM_ERR_TIMEOUT at the next synchronisation instead of hanging).  Runs
+ * three barriers over nblocks CTAs (cooperative launch, so nblocks must fit
+ * on the device at once); starve != 0 starts the arrival count where no CTA
+ * can complete it, so every wait runs out.  *timed_out (host) = 1 if a wait
+ * gave up.  ERR_ARG for nblocks < 1, ERR_CUDA if the launch fails.
+ * Synchronises the device. */
+int tdbem_grid_barrier_probe(int32_t nblocks, int32_t starve, int32_t *timed_out);
+
 /* Learned sparse approximate inverse for the zero-lag solve (an addition
  * of this library; the paper only states that the system is sparse).  A
  * trainer holds a 2-layer network (5*width inputs -> hidden ReLU -> width

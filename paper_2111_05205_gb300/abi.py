@@ -90,6 +90,7 @@ SIGNATURES = {
     "tdbem_reset_stats": (ctypes.c_int, [_P]),
     "tdbem_sync": (ctypes.c_int, [_P]),
     "tdbem_zero_lag_solve_static": (ctypes.c_int, [_P, _P, _P, _I]),
+    "tdbem_grid_barrier_probe": (ctypes.c_int, [_I, _I, ctypes.POINTER(_I)]),
 }
 
 _lib = None
@@ -363,3 +364,12 @@ def tdbem_zero_lag_solve_static(ctx, b, x, on_device=False):
     """Solve A x = b with no device allocation (see include/tdbem.h).
     b, x: numpy arrays (host) or torch CUDA tensors (on_device)."""
     _check(ctx, lib().tdbem_zero_lag_solve_static(ctx, _ptr(b), _ptr(x), int(bool(on_device))))
+
+
+def tdbem_grid_barrier_probe(nblocks, starve):
+    """Run the bounded grid barrier self-check; True if a wait gave up."""
+    out = _I()
+    code = lib().tdbem_grid_barrier_probe(int(nblocks), int(starve), ctypes.byref(out))
+    if code != TDBEM_OK:
+        raise TdbemError(code, "tdbem_grid_barrier_probe")
+    return bool(out.value)

@@ -128,6 +128,13 @@ int check_flags(tdbem_ctx *c)
     int f = 0;
     TD_CUDA(cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f & 1) return fail(c, TDBEM_ERR_DIVERGED, "non-finite solution value (divergence guard)");
+    if (f & 4) {
+        // a grid barrier of the fused solve gave up waiting: reset it and
+        // solve with one launch per sweep from now on
+        cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
+        c->jac_grid = 0;
+        return fail(c, TDBEM_ERR_TIMEOUT, "zero-lag solve: grid barrier timed out");
+    }
     return TDBEM_OK;
 }
 
@@ -456,6 +463,8 @@ int tdbem_prepare(tdbem_ctx *c)
     TD_CUDA(dalloc(c, &c->d_b, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xa, (size_t)ns));
     TD_CUDA(dalloc(c, &c->d_xb, (size_t)ns));
+    TD_CUDA(dalloc(c, &c->d_bar, 2));
+    TD_CUDA(setup_jacobi_fused(c));
     TD_CUDA(dalloc(c, &c->d_r, (size_t)ns));
     TD_CUDA(cudaMemsetAsync(c->d_b, 0, ns * sizeof(double), c->s));
     TD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->s));
@@ -496,12 +505,14 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
             PhaseTimer t(c, PH_SOLVE);
             if (c->sai_val) {
                 for (int it = 0; it < c->sai_iters; ++it) TD_CUDA(launch_sai_sweep(c, alpha, it));
+            } else if (c->jac_grid > 0) {
+                TD_CUDA(launch_jacobi_fused(c, alpha));
             } else {
                 for (int it = 0; it < c->solve_iters; ++it)
                     TD_CUDA(launch_jacobi(c, alpha, it, it == c->solve_iters - 1));
             }
         }
-        c->launches[PH_SOLVE] += c->sai_val ? c->sai_iters : c->solve_iters;
+        c->launches[PH_SOLVE] += c->sai_val ? c->sai_iters : (c->jac_grid > 0 ? 1 : c->solve_iters);
         c->alpha = alpha;
         c->steps_total += 1;
     }

@@ -404,10 +404,38 @@ cudaError_t launch_split_histories(tdbem_ctx *c)
     return cudaGetLastError();
 }
 
-// One Jacobi sweep x' = D^-1 (b - R x) of the zero-lag system (A = D + R,
-// R in the ELL store).  it = 0 starts from x = D^-1 b.  The last sweep adds
-// the solution to the unknown component of step a-1 (u where phi = 1, q
-// where phi = 0) and flags a non-finite value (flag bit 1).
+// One row of a Jacobi sweep x' = D^-1 (b - R x) of the zero-lag system
+// (A = D + R, R in the ELL store); xin = nullptr starts from x = D^-1 b.
+// LDX loads an entry of x (the fused kernel reads past L2 coherence points).
+// Shared by the one-sweep and the fused kernels, so both give the same bits.
+template <typename LDX>
+__device__ __forceinline__ double jacobi_row(int i, int ns, int width, const double *__restrict__ aoff,
+                                             const int32_t *__restrict__ acol, const double *__restrict__ ainv,
+                                             const double *__restrict__ b, const double *xin, LDX ldx)
+{
+    double s = b[i];
+    if (xin) {
+        for (int k = 0; k < width; ++k) {
+            int cidx = acol[(int64_t)k * ns + i];
+            if (cidx >= 0) s -= aoff[(int64_t)k * ns + i] * ldx(xin + cidx);
+        }
+    }
+    return s * ainv[i];
+}
+
+// The last sweep adds the solution to the unknown component of step a-1 (u
+// where phi = 1, q where phi = 0) and flags a non-finite value (flag bit 1).
+__device__ __forceinline__ void jacobi_store(int i, double x, int64_t row, const int8_t *__restrict__ phi, double *u,
+                                             double *q, float2 *us, float2 *qs, int *flag)
+{
+    double *h = phi[i] ? u : q;
+    double v = h[row + i] + x;
+    h[row + i] = v;
+    if (us) (phi[i] ? us : qs)[row + i] = split2(v);
+    if (!isfinite(x)) atomicOr(flag, 1);
+}
+
+// One Jacobi sweep; it = 0 starts from x = D^-1 b, the last one stores.
 __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, const int32_t *__restrict__ acol,
                          const double *__restrict__ ainv, const double *__restrict__ b,
                          const double *__restrict__ xin, double *xout, int last, int64_t row,
@@ -421,23 +449,102 @@ __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, con
         if (a > alim) return;  // instance past its last step
         row = (int64_t)(a - 1) * ns;
     }
-    double s = b[i];
-    if (xin) {
-        for (int k = 0; k < width; ++k) {
-            int cidx = acol[(int64_t)k * ns + i];
-            if (cidx >= 0) s -= aoff[(int64_t)k * ns + i] * xin[cidx];
-        }
-    }
-    double x = s * ainv[i];
-    if (last) {
-        double *h = phi[i] ? u : q;
-        double v = h[row + i] + x;
-        h[row + i] = v;
-        if (us) (phi[i] ? us : qs)[row + i] = split2(v);
-        if (!isfinite(x)) atomicOr(flag, 1);
-    } else {
+    const double x = jacobi_row(i, ns, width, aoff, acol, ainv, b, xin, [](const double *p) { return *p; });
+    if (last)
+        jacobi_store(i, x, row, phi, u, q, us, qs, flag);
+    else
         xout[i] = x;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): arrival
+// counter bar[0], generation bar[1].  The wait is bounded: after
+// kBarrierPolls polls the CTA records a timeout (flag bit 4) and goes on,
+// so a barrier that cannot complete ends the kernel with an error that the
+// host reports, never with a hang.
+constexpr unsigned kBarrierSpins = 1u << 12;  // polls without a sleep
+constexpr unsigned kBarrierPolls = 1u << 22;  // then with 64 ns sleeps: about 0.3 s in all
+
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            // spin first (the other CTAs are a sweep of a few microseconds
+            // away), then poll with short sleeps
+            unsigned polls = 0;
+            while (*gen == g) {
+                if (++polls > kBarrierPolls) {
+                    atomicOr(flag, 4);
+                    break;
+                }
+                if (polls > kBarrierSpins) __nanosleep(64);
+            }
+        }
+        __threadfence();
     }
+    __syncthreads();
+}
+
+// All K sweeps of one step in one cooperative launch (rows grid-strided),
+// with a grid barrier between sweeps; the same ping-pong buffers and row
+// arithmetic as K launches of k_jacobi.  x is read with ld.global.cg: a CTA
+// must not see an earlier sweep's value from its own L1.
+__global__ void __launch_bounds__(256) k_jacobi_fused(int ns, int width, const double *__restrict__ aoff,
+                                                      const int32_t *__restrict__ acol,
+                                                      const double *__restrict__ ainv, const double *__restrict__ b,
+                                                      double *xa, double *xb, int K, int64_t row,
+                                                      const int8_t *__restrict__ phi, double *u, double *q,
+                                                      float2 *us, float2 *qs, int *flag, unsigned *bar)
+{
+    for (int it = 0; it < K; ++it) {
+        const double *xin = (it == 0) ? nullptr : ((it & 1) ? xa : xb);
+        double *xout = (it & 1) ? xb : xa;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+            const double x = jacobi_row(i, ns, width, aoff, acol, ainv, b, xin, [](const double *p) { return __ldcg(p); });
+            if (it == K - 1)
+                jacobi_store(i, x, row, phi, u, q, us, qs, flag);
+            else
+                xout[i] = x;
+        }
+        if (it < K - 1) grid_barrier(bar, flag);
+    }
+}
+
+// Three grid barriers in a row (the probe of the bounded wait below).
+__global__ void k_barrier_probe(unsigned *bar, int *flag, int rounds)
+{
+    for (int r = 0; r < rounds; ++r) grid_barrier(bar, flag);
+}
+
+cudaError_t setup_jacobi_fused(tdbem_ctx *c)
+{
+    c->jac_grid = 0;
+    int coop = 0, nsm = 0, per = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_fused, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || per < 1 || !c->d_bar) return cudaSuccess;  // K one-sweep launches instead
+    e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->s);
+    if (e != cudaSuccess) return e;
+    c->jac_grid = (int)std::min<int64_t>(((int64_t)c->ns + 255) / 256, (int64_t)per * nsm);
+    return cudaSuccess;
+}
+
+cudaError_t launch_jacobi_fused(tdbem_ctx *c, int alpha)
+{
+    int ns = c->ns, width = c->ell_w, K = c->solve_iters;
+    int64_t row = (int64_t)(alpha - 1) * c->ns;
+    void *args[] = {&ns, &width, &c->d_aoff, &c->d_acol, &c->d_ainv, &c->d_b, &c->d_xa, &c->d_xb, &K, &row,
+                    &c->d_phi, &c->d_u, &c->d_q, &c->d_us, &c->d_qs, &c->d_flag, &c->d_bar};
+    return cudaLaunchCooperativeKernel((const void *)k_jacobi_fused, dim3(c->jac_grid), dim3(256), args, 0, c->s);
 }
 
 cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last)
@@ -483,3 +590,29 @@ cudaError_t launch_gather_x(tdbem_ctx *c, int a0, int nsteps, double *x)
 }
 
 }  // namespace tdbem
+
+extern "C" int tdbem_grid_barrier_probe(int32_t nblocks, int32_t starve, int32_t *timed_out)
+{
+    using namespace tdbem;
+    if (nblocks < 1 || !timed_out) return TDBEM_ERR_ARG;
+    *timed_out = 0;
+    unsigned *bar = nullptr;
+    int *flag = nullptr;
+    cudaError_t e = cudaMalloc(&bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&flag, sizeof(int));
+    // starve: an arrival count no CTA can complete, so every wait runs out
+    const unsigned init[2] = {starve ? 0x80000000u : 0u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpy(bar, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(int));
+    int rounds = 3;
+    void *args[] = {&bar, &flag, &rounds};
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3(nblocks), dim3(32), args, 0, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int f = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(bar);
+    cudaFree(flag);
+    if (e != cudaSuccess) return TDBEM_ERR_CUDA;
+    *timed_out = (f & 4) ? 1 : 0;
+    return TDBEM_OK;
+}

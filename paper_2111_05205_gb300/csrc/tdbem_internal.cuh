@@ -167,6 +167,8 @@ struct tdbem_ctx {
     float2 *d_us = nullptr, *d_qs = nullptr; // [nt][ns] float-pair copies (split only)
     double *d_b = nullptr, *d_xa = nullptr, *d_xb = nullptr;
     int ell_w = 0;               // off-diagonal entries per row of the zero-lag store
+    int jac_grid = 0;            // CTAs of the fused Jacobi launch (0: one launch per sweep)
+    unsigned *d_bar = nullptr;   // its grid barrier: arrival count, generation
     double *d_aoff = nullptr;    // [ell_w][ns]
     int32_t *d_acol = nullptr;   // [ell_w][ns]
     double *d_ainv = nullptr;    // [ns]
@@ -227,6 +229,8 @@ void free_tree(tdbem_ctx *c);
 // Kernel launchers (march.cu)
 cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far);
 cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last);
+cudaError_t setup_jacobi_fused(tdbem_ctx *c);
+cudaError_t launch_jacobi_fused(tdbem_ctx *c, int alpha);
 cudaError_t launch_gather_x(tdbem_ctx *c, int a0, int nsteps, double *x);
 cudaError_t launch_alpha_next(tdbem_ctx *c);
 cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it);
