@@ -135,6 +135,17 @@ def _timed(abi, torch, ctx, nsteps):
     return e0.elapsed_time(e1)
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the whole job is done only when every rank
+    is (dist = torch.distributed, or None for one process)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     from paper_2111_05205_gb300 import Solver, abi, build
@@ -185,10 +196,7 @@ def run_ours(args):
         dist.barrier()
     st = s.stats()
     abi.tdbem_sync(ctx)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / args.steps
 
     # end to end through the C ABI with host buffers: per step, the
@@ -483,7 +491,8 @@ def run_reference(args):
     out = {"metric": METRIC, "value": 1.0 / per_step, "unit": "time-steps/s", "n_gpus": 0,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload + "_direct_fp64", "ns": w.ns},
+           "config": {"workload": args.workload + "_direct_" + args.precision, "ns": w.ns,
+                      "oracle": "direct FP64 history sum (the same workload and steps)"},
            "cpu_baseline": {"value": 1.0 / per_step, "unit": "time-steps/s", "cores": o.cores,
                             "kind": "oracle", "sample": o.sample},
            "e2e": {"value": 1.0 / per_step, "unit": "time-steps/s", "h2d_bytes_per_step": 0,
