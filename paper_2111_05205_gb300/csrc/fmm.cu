@@ -470,6 +470,15 @@ __global__ void k_to_float(int64_t n, const double *__restrict__ a, float *b)
         b[e] = (float)a[e];
 }
 
+// Exact sum of two floats (two-sum of Knuth): a + b = s + e.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
+{
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+
 template <typename TC>
 __global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
                              const int64_t *__restrict__ oidx, const TC *__restrict__ C, double *ring, double *G)
@@ -478,7 +487,10 @@ __global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, 
     // list holds at most 189 cells), so the operand loads do not wait on
     // index loads.  Each thread sums 4 consecutive entries (one 16-byte load
     // per column when R = nblk P is a multiple of 4) over the cell's columns
-    // in list order, 8 columns' loads at a time.
+    // in list order, 8 columns' loads at a time.  FP32 columns are summed in
+    // double-float (a float pair with two-sum updates, about 48 bits): the
+    // far field cancels terms 1e4-1e5 larger than itself, so a plain FP32
+    // sum is not enough, and FP64 adds are 57 times slower on this GPU.
     __shared__ int64_t cols[kMaxIL];
     const int R = nblk * P;
     const int O = blockIdx.x;
@@ -489,6 +501,7 @@ __global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, 
     for (int e0 = 4 * threadIdx.x; e0 < R; e0 += 4 * blockDim.x) {
         double s[4] = {0.0, 0.0, 0.0, 0.0};
         if ((R & 3) == 0 && sizeof(TC) == 4) {
+            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
             int t = 0;
             for (; t + 8 <= nt; t += 8) {
                 float4 f[8];
@@ -496,19 +509,20 @@ __global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, 
                 for (int v = 0; v < 8; ++v) f[v] = *reinterpret_cast<const float4 *>(C + cols[t + v] + e0);
 #pragma unroll
                 for (int v = 0; v < 8; ++v) {
-                    s[0] += f[v].x;
-                    s[1] += f[v].y;
-                    s[2] += f[v].z;
-                    s[3] += f[v].w;
+                    two_sum_acc(hi[0], lo[0], f[v].x);
+                    two_sum_acc(hi[1], lo[1], f[v].y);
+                    two_sum_acc(hi[2], lo[2], f[v].z);
+                    two_sum_acc(hi[3], lo[3], f[v].w);
                 }
             }
             for (; t < nt; ++t) {
                 const float4 f = *reinterpret_cast<const float4 *>(C + cols[t] + e0);
-                s[0] += f.x;
-                s[1] += f.y;
-                s[2] += f.z;
-                s[3] += f.w;
+                two_sum_acc(hi[0], lo[0], f.x);
+                two_sum_acc(hi[1], lo[1], f.y);
+                two_sum_acc(hi[2], lo[2], f.z);
+                two_sum_acc(hi[3], lo[3], f.w);
             }
+            for (int q = 0; q < 4; ++q) s[q] = (double)hi[q] + (double)lo[q];
         } else {
             for (int q = 0; q < 4 && e0 + q < R; ++q)
                 for (int t = 0; t < nt; ++t) s[q] += (double)C[cols[t] + e0 + q];

@@ -353,7 +353,10 @@ static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, c
     auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, WPR> : k_near_sum<true, false, SPLIT, WPR>)
                 : (hw ? k_near_sum<false, true, SPLIT, WPR> : k_near_sum<false, false, SPLIT, WPR>);
     constexpr int rows = kNearWarps / WPR;
-    k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, c->d_col, c->d_rowblk, c->d_meta, c->d_boff,
+    // the kernel uses a pair's column only to address the history: in the
+    // split form with near lists that is the column's sorted position
+    const int32_t *hcol = (SPLIT && c->d_hcol) ? c->d_hcol : c->d_col;
+    k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, hcol, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
                                        c->d_n, d_far, c->P.nt - 1, c->d_b);
     return cudaGetLastError();
@@ -383,10 +386,15 @@ __global__ void k_split_inplace(int64_t n, double *v)
 }
 
 // Float-pair copies of FP64 values.
-__global__ void k_split_copy(int64_t n, const double *__restrict__ v, float2 *out)
+// out = the float-pair copy of v ([nt][ns]); with hpos, element i of a
+// step goes to position hpos[i] of that step's row.
+__global__ void k_split_copy(int64_t n, int ns, const double *__restrict__ v, const int32_t *__restrict__ hpos,
+                             float2 *out)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = split2(v[k]);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k % ns;
+        out[hpos ? k - i + hpos[i] : k] = split2(v[k]);
+    }
 }
 
 cudaError_t launch_split_coefficients(tdbem_ctx *c)
@@ -399,8 +407,8 @@ cudaError_t launch_split_coefficients(tdbem_ctx *c)
 cudaError_t launch_split_histories(tdbem_ctx *c)
 {
     int64_t n = (int64_t)c->P.nt * c->ns;
-    k_split_copy<<<152 * 16, 256, 0, c->s>>>(n, c->d_u, c->d_us);
-    k_split_copy<<<152 * 16, 256, 0, c->s>>>(n, c->d_q, c->d_qs);
+    k_split_copy<<<152 * 16, 256, 0, c->s>>>(n, c->ns, c->d_u, c->d_hpos, c->d_us);
+    k_split_copy<<<152 * 16, 256, 0, c->s>>>(n, c->ns, c->d_q, c->d_hpos, c->d_qs);
     return cudaGetLastError();
 }
 
@@ -425,13 +433,16 @@ __device__ __forceinline__ double jacobi_row(int i, int ns, int width, const dou
 
 // The last sweep adds the solution to the unknown component of step a-1 (u
 // where phi = 1, q where phi = 0) and flags a non-finite value (flag bit 1).
+// The float-pair copy holds element i at position hpos[i] (identity when
+// hpos is null).
 __device__ __forceinline__ void jacobi_store(int i, double x, int64_t row, const int8_t *__restrict__ phi, double *u,
-                                             double *q, float2 *us, float2 *qs, int *flag)
+                                             double *q, float2 *us, float2 *qs, const int32_t *__restrict__ hpos,
+                                             int *flag)
 {
     double *h = phi[i] ? u : q;
     double v = h[row + i] + x;
     h[row + i] = v;
-    if (us) (phi[i] ? us : qs)[row + i] = split2(v);
+    if (us) (phi[i] ? us : qs)[row + (hpos ? hpos[i] : i)] = split2(v);
     if (!isfinite(x)) atomicOr(flag, 1);
 }
 
@@ -440,7 +451,7 @@ __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, con
                          const double *__restrict__ ainv, const double *__restrict__ b,
                          const double *__restrict__ xin, double *xout, int last, int64_t row,
                          const int *__restrict__ alpha_dev, const int8_t *__restrict__ phi, double *u, double *q,
-                         float2 *us, float2 *qs, int alim, int *flag)
+                         float2 *us, float2 *qs, const int32_t *__restrict__ hpos, int alim, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
@@ -451,7 +462,7 @@ __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, con
     }
     const double x = jacobi_row(i, ns, width, aoff, acol, ainv, b, xin, [](const double *p) { return *p; });
     if (last)
-        jacobi_store(i, x, row, phi, u, q, us, qs, flag);
+        jacobi_store(i, x, row, phi, u, q, us, qs, hpos, flag);
     else
         xout[i] = x;
 }
@@ -461,8 +472,7 @@ __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, con
 // kBarrierPolls polls the CTA records a timeout (flag bit 4) and goes on,
 // so a barrier that cannot complete ends the kernel with an error that the
 // host reports, never with a hang.
-constexpr unsigned kBarrierSpins = 1u << 12;  // polls without a sleep
-constexpr unsigned kBarrierPolls = 1u << 22;  // then with 64 ns sleeps: about 0.3 s in all
+constexpr unsigned kBarrierPolls = 1u << 22;  // with 64 ns sleeps: about 0.3 s
 
 __device__ __forceinline__ void grid_barrier(unsigned *bar, int *flag)
 {
@@ -476,15 +486,15 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, int *flag)
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
-            // spin first (the other CTAs are a sweep of a few microseconds
-            // away), then poll with short sleeps
+            // poll with short sleeps (polling without them measured slower:
+            // every waiting CTA then hammers the same word)
             unsigned polls = 0;
             while (*gen == g) {
                 if (++polls > kBarrierPolls) {
                     atomicOr(flag, 4);
                     break;
                 }
-                if (polls > kBarrierSpins) __nanosleep(64);
+                __nanosleep(64);
             }
         }
         __threadfence();
@@ -501,7 +511,8 @@ __global__ void __launch_bounds__(256) k_jacobi_fused(int ns, int width, const d
                                                       const double *__restrict__ ainv, const double *__restrict__ b,
                                                       double *xa, double *xb, int K, int64_t row,
                                                       const int8_t *__restrict__ phi, double *u, double *q,
-                                                      float2 *us, float2 *qs, int *flag, unsigned *bar)
+                                                      float2 *us, float2 *qs, const int32_t *__restrict__ hpos,
+                                                      int *flag, unsigned *bar)
 {
     for (int it = 0; it < K; ++it) {
         const double *xin = (it == 0) ? nullptr : ((it & 1) ? xa : xb);
@@ -509,7 +520,7 @@ __global__ void __launch_bounds__(256) k_jacobi_fused(int ns, int width, const d
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
             const double x = jacobi_row(i, ns, width, aoff, acol, ainv, b, xin, [](const double *p) { return __ldcg(p); });
             if (it == K - 1)
-                jacobi_store(i, x, row, phi, u, q, us, qs, flag);
+                jacobi_store(i, x, row, phi, u, q, us, qs, hpos, flag);
             else
                 xout[i] = x;
         }
@@ -543,7 +554,7 @@ cudaError_t launch_jacobi_fused(tdbem_ctx *c, int alpha)
     int ns = c->ns, width = c->ell_w, K = c->solve_iters;
     int64_t row = (int64_t)(alpha - 1) * c->ns;
     void *args[] = {&ns, &width, &c->d_aoff, &c->d_acol, &c->d_ainv, &c->d_b, &c->d_xa, &c->d_xb, &K, &row,
-                    &c->d_phi, &c->d_u, &c->d_q, &c->d_us, &c->d_qs, &c->d_flag, &c->d_bar};
+                    &c->d_phi, &c->d_u, &c->d_q, &c->d_us, &c->d_qs, &c->d_hpos, &c->d_flag, &c->d_bar};
     return cudaLaunchCooperativeKernel((const void *)k_jacobi_fused, dim3(c->jac_grid), dim3(256), args, 0, c->s);
 }
 
@@ -554,7 +565,7 @@ cudaError_t launch_jacobi(tdbem_ctx *c, int alpha, int it, int last)
     int64_t row = (int64_t)(alpha - 1) * c->ns;
     k_jacobi<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->ell_w, c->d_aoff, c->d_acol, c->d_ainv, c->d_b, xin, xout, last,
                                                    row, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_phi, c->d_u,
-                                                   c->d_q, c->d_us, c->d_qs, c->P.nt - 1, c->d_flag);
+                                                   c->d_q, c->d_us, c->d_qs, c->d_hpos, c->P.nt - 1, c->d_flag);
     return cudaGetLastError();
 }
 

@@ -242,7 +242,8 @@ __global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__
                             const double *__restrict__ aoff, const int32_t *__restrict__ acol,
                             const double *__restrict__ ainv, const double *__restrict__ b,
                             const double *__restrict__ x, double *xout, int last, int64_t row,
-                            const int8_t *__restrict__ phi, double *u, double *q, float2 *us, float2 *qs, int *flag)
+                            const int8_t *__restrict__ phi, double *u, double *q, float2 *us, float2 *qs,
+                            const int32_t *__restrict__ hpos, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
@@ -266,7 +267,7 @@ __global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__
         hh[row + i] = v;
         if (us) {
             float hi = __double2float_rn(v);
-            (phi[i] ? us : qs)[row + i] = make_float2(hi, __double2float_rn(v - (double)hi));
+            (phi[i] ? us : qs)[row + (hpos ? hpos[i] : i)] = make_float2(hi, __double2float_rn(v - (double)hi));
         }
         if (!isfinite(s)) atomicOr(flag, 1);
     } else {
@@ -519,7 +520,7 @@ cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it)
     int64_t row = (int64_t)(alpha - 1) * ns;
     k_sai_sweep<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->sai_w, c->ell_w, c->sai_val, c->sai_col, c->d_aoff,
                                                     c->d_acol, c->d_ainv, c->d_b, xin, xout, last, row, c->d_phi,
-                                                    c->d_u, c->d_q, c->d_us, c->d_qs, c->d_flag);
+                                                    c->d_u, c->d_q, c->d_us, c->d_qs, c->d_hpos, c->d_flag);
     return cudaGetLastError();
 }
 

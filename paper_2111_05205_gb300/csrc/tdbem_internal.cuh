@@ -165,6 +165,11 @@ struct tdbem_ctx {
     double *d_u = nullptr, *d_q = nullptr;  // [nt][ns] histories
     bool split = false;                     // split-precision history sum
     float2 *d_us = nullptr, *d_qs = nullptr; // [nt][ns] float-pair copies (split only)
+    // split form with near lists (FMM): the float-pair copies hold element
+    // perm[p] at position p (the octree's Morton order), so a near list's
+    // history gathers are contiguous runs; d_hpos[i] = position of element i,
+    // d_hcol = the near pairs' columns as positions (nullptr otherwise)
+    int32_t *d_hpos = nullptr, *d_hcol = nullptr;
     double *d_b = nullptr, *d_xa = nullptr, *d_xb = nullptr;
     int ell_w = 0;               // off-diagonal entries per row of the zero-lag store
     int jac_grid = 0;            // CTAs of the fused Jacobi launch (0: one launch per sweep)

@@ -324,7 +324,8 @@ __global__ void k_near_count(int ns, const int32_t *__restrict__ e2c, const int3
 
 __global__ void k_near_fill(int ns, const int32_t *__restrict__ e2c, const int32_t *__restrict__ nbr,
                             const int32_t *__restrict__ ncount, const int32_t *__restrict__ cstart,
-                            const int32_t *__restrict__ perm, const int64_t *__restrict__ prow, int32_t *col)
+                            const int32_t *__restrict__ perm, const int64_t *__restrict__ prow, int32_t *col,
+                            int32_t *hcol)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
@@ -332,8 +333,17 @@ __global__ void k_near_fill(int ns, const int32_t *__restrict__ e2c, const int32
     int64_t o = prow[i];
     for (int a = 0; a < ncount[c]; ++a) {
         int m = nbr[(int64_t)c * 27 + a];
-        for (int p = cstart[m]; p < cstart[m + 1]; ++p) col[o++] = perm[p];
+        for (int p = cstart[m]; p < cstart[m + 1]; ++p) {
+            if (hcol) hcol[o] = p;  // the element's position in the sorted order
+            col[o++] = perm[p];
+        }
     }
+}
+
+__global__ void k_invert_perm(int ns, const int32_t *__restrict__ perm, int32_t *pos)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < ns) pos[perm[p]] = p;
 }
 
 cudaError_t build_near_lists(tdbem_ctx *c)
@@ -371,10 +381,21 @@ cudaError_t build_near_lists(tdbem_ctx *c)
     c->d_prow = (int64_t *)p1;
     c->d_rowblk = (int64_t *)p2;
     c->d_col = (int32_t *)p3;
+    if (c->split) {
+        // the split form's float-pair histories are kept in the sorted order
+        void *p4, *p5;
+        if ((e = cudaMalloc(&p4, std::max<int64_t>(c->npairs, 1) * sizeof(int32_t))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&p5, ns * sizeof(int32_t))) != cudaSuccess) return e;
+        c->allocs.push_back(p4);
+        c->allocs.push_back(p5);
+        c->d_hcol = (int32_t *)p4;
+        c->d_hpos = (int32_t *)p5;
+        k_invert_perm<<<(ns + 255) / 256, 256, 0, s>>>(ns, c->tree.perm, c->d_hpos);
+    }
     cudaMemcpyAsync(c->d_prow, prow.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_rowblk, rowblk.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     k_near_fill<<<(ns + 127) / 128, 128, 0, s>>>(ns, e2c, T.nbr, T.ncount, T.cstart, c->tree.perm, c->d_prow,
-                                                c->d_col);
+                                                c->d_col, c->d_hcol);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
 }
