@@ -215,7 +215,7 @@ __device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_
     if (p < end) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-template <bool HU, bool HW, bool SPLIT, int WPR>
+template <bool HU, bool HW, bool SPLIT, int WPR, bool COL>
 __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const int64_t *__restrict__ prow,
                                          const int32_t *__restrict__ col, const int64_t *__restrict__ rowblk,
                                          const uint16_t *__restrict__ meta, const int64_t *__restrict__ boff,
@@ -239,7 +239,7 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
     const int64_t p0 = prow[i];
     const int npr = (int)(prow[i + 1] - p0);
     const uint16_t *mrow = meta + p0;
-    const int32_t *crow = col ? col + p0 : nullptr;
+    const int32_t *crow = COL ? col + p0 : nullptr;  // COL: explicit columns (near lists), else j = pair index
     const int64_t *orow = boff + rowblk[i];
     const int nblk = (int)(rowblk[i + 1] - rowblk[i]);
     const V *kuv = reinterpret_cast<const V *>(ku);
@@ -253,14 +253,16 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
             if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
         }
     }
-    // metadata of the first block; the next block's is fetched while the
-    // current one is summed
+    // metadata and columns of the first block; the next block's are fetched
+    // while the current one is summed
     int bk = wr;
     unsigned mnext = 0u;
     int64_t onext = 0;
+    int jnext = 0;
     if (bk < nblk) {
         const int pr = bk * 32 + lane;
         mnext = (pr < npr) ? mrow[pr] : 0u;
+        if constexpr (COL) jnext = (pr < npr) ? crow[pr] : 0;
         onext = orow[bk];
     }
     for (; bk < nblk; bk += W) {
@@ -271,14 +273,14 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
                 if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
             }
         }
-        const int pr = bk * 32 + lane;
-        const int j = (pr < npr) ? (crow ? crow[pr] : pr) : 0;
+        const int j = COL ? jnext : ((bk * 32 + lane < npr) ? bk * 32 + lane : 0);
         const unsigned m = mnext;
         const int64_t o = onext;
         const int nb = bk + W;
         if (nb < nblk) {
             const int pn = nb * 32 + lane;
             mnext = (pn < npr) ? mrow[pn] : 0u;
+            if constexpr (COL) jnext = (pn < npr) ? crow[pn] : 0;
             onext = orow[nb];
         }
         // cnt = 0 past the row's end; lag g = g0 + s reaches back to
@@ -298,7 +300,7 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
 // SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
 // coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
 // are read from their float-pair copies and the sum runs in double-float.
-template <bool HU, bool HW, bool SPLIT, int WPR>
+template <bool HU, bool HW, bool SPLIT, int WPR, bool COL>
 __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
                                                               const int64_t *__restrict__ prow,
                                                               const int32_t *__restrict__ col,
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
     const int i = blockIdx.x * (kNearWarps / WPR) + warp / WPR, wr = warp % WPR;
     double acc = 0.0;
     DF dacc = {0.f, 0.f};
-    if (i < ns) near_row<HU, HW, SPLIT, WPR>(i, wr, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
+    if (i < ns) near_row<HU, HW, SPLIT, WPR, COL>(i, wr, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
     if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
@@ -346,12 +348,12 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
     }
 }
 
-template <bool SPLIT, int WPR>
+template <bool SPLIT, int WPR, bool COL>
 static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
     bool hu = c->d_ku != nullptr, hw = c->d_kw != nullptr;
-    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, WPR> : k_near_sum<true, false, SPLIT, WPR>)
-                : (hw ? k_near_sum<false, true, SPLIT, WPR> : k_near_sum<false, false, SPLIT, WPR>);
+    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, WPR, COL> : k_near_sum<true, false, SPLIT, WPR, COL>)
+                : (hw ? k_near_sum<false, true, SPLIT, WPR, COL> : k_near_sum<false, false, SPLIT, WPR, COL>);
     constexpr int rows = kNearWarps / WPR;
     // the kernel uses a pair's column only to address the history: in the
     // split form with near lists that is the column's sorted position
@@ -364,10 +366,15 @@ static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, c
 
 cudaError_t launch_near_sum(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
+    // all pairs (no column list): long rows, four warps each
+    if (!c->d_col)
+        return c->split ? near_dispatch<true, kNearWarps, false>(c, alpha, d_exc, d_far)
+                        : near_dispatch<false, kNearWarps, false>(c, alpha, d_exc, d_far);
     if (c->near_wpr == 1)
-        return c->split ? near_dispatch<true, 1>(c, alpha, d_exc, d_far) : near_dispatch<false, 1>(c, alpha, d_exc, d_far);
-    return c->split ? near_dispatch<true, kNearWarps>(c, alpha, d_exc, d_far)
-                    : near_dispatch<false, kNearWarps>(c, alpha, d_exc, d_far);
+        return c->split ? near_dispatch<true, 1, true>(c, alpha, d_exc, d_far)
+                        : near_dispatch<false, 1, true>(c, alpha, d_exc, d_far);
+    return c->split ? near_dispatch<true, kNearWarps, true>(c, alpha, d_exc, d_far)
+                    : near_dispatch<false, kNearWarps, true>(c, alpha, d_exc, d_far);
 }
 
 __device__ __forceinline__ float2 split2(double v)
