@@ -318,50 +318,6 @@ __global__ void k_l2l(int ps, int pt, int ncp, const uint64_t *__restrict__ pkey
     for (int e = threadIdx.x; e < P; e += blockDim.x) Lc[(int64_t)c * P + e] += b0[e];
 }
 
-// M2L at one level for source interval k (Algorithm 1, near-future part and
-// the derivative contributions): for every observation cell O (blockIdx.x)
-// and operator block blk (blockIdx.y), Y = sum_{S in IL(O)} op[off(O,S)][blk] M(S);
-// blk <= mu goes to the local of I_{k+blk+1} (ring slot), blk > mu to
-// G_p (p = blk - mu), the contribution L^(p)_{k+mu+1,k} of Eq. L_l,k.
-__global__ void k_m2l_apply(int P, int nblk, int mu, int lev, int nc, const uint64_t *__restrict__ ckey,
-                            const int32_t *__restrict__ il, const int32_t *__restrict__ ilcount,
-                            const double *__restrict__ M, const double *__restrict__ op, double *ring, int nslot,
-                            int k, double *G)
-{
-    extern __shared__ double sm[];
-    int O = blockIdx.x, blk = blockIdx.y;
-    int co[3] = {0, 0, 0};
-    for (int b = 0; b < lev; ++b)
-        for (int a = 0; a < 3; ++a) co[a] |= (int)((ckey[O] >> (3 * b + a)) & 1u) << b;
-    double acc[8];
-    for (int r = 0; r < 8; ++r) acc[r] = 0.0;
-    for (int t = 0; t < ilcount[O]; ++t) {
-        int S = il[(int64_t)O * 189 + t];
-        int cs[3] = {0, 0, 0};
-        for (int b = 0; b < lev; ++b)
-            for (int a = 0; a < 3; ++a) cs[a] |= (int)((ckey[S] >> (3 * b + a)) & 1u) << b;
-        int o = (cs[0] - co[0] + 3) + 7 * ((cs[1] - co[1] + 3) + 7 * (cs[2] - co[2] + 3));
-        __syncthreads();
-        for (int e = threadIdx.x; e < P; e += blockDim.x) sm[e] = M[(int64_t)S * P + e];
-        __syncthreads();
-        const double *A = op + ((int64_t)o * nblk + blk) * P * P;
-        for (int r = threadIdx.x, q = 0; r < P; r += blockDim.x, ++q) {
-            double s = 0.0;
-            const double *row = A + (int64_t)r * P;
-            for (int cI = 0; cI < P; ++cI) s += row[cI] * sm[cI];
-            acc[q] += s;
-        }
-    }
-    for (int r = threadIdx.x, q = 0; r < P; r += blockDim.x, ++q) {
-        if (blk <= mu) {
-            int slot = (k + blk + 1) % nslot;
-            ring[((int64_t)slot * nc + O) * P + r] += acc[q];
-        } else {
-            G[((int64_t)(blk - mu - 1) * nc + O) * P + r] = acc[q];
-        }
-    }
-}
-
 // Distant-future recurrences of Formula 1 (Eq. m2l_expand_rec1, Eq. m2l_rec,
 // Eq. m2l_expand_rec2) for every entry of every cell of one level:
 //   D_p <- D_p + G_p + sum_{m<=p-2} c_m^p(k) A_{p,m}
