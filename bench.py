@@ -426,20 +426,25 @@ def fp64_form(args, w, phi, stream):
 
 
 def _kernel_rev():
-    """Source revision of the history-sum kernel: a hash of its part of
-    csrc/march.cu (the file up to the end of its launcher: constants,
-    incident term, double-float helpers, kernel) and of
-    csrc/tdbem_internal.cuh."""
+    """Source revision of the history-sum kernel: a hash of the code (line
+    comments and blank lines dropped) of its part of csrc/march.cu (the file
+    up to the end of its launcher: constants, incident term, double-float
+    helpers, kernel) and of csrc/tdbem_internal.cuh."""
     import hashlib
+    import re
+
+    def code(text):
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.split("\n"))
+        return "\n".join(ln for ln in lines if ln)
+
     h = hashlib.sha1()
     with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", "march.cu")) as fh:
         src = fh.read()
-    a = 0
     b = src.index("cudaError_t launch_near_sum(")
     b = src.index("\n}\n", b)
-    h.update(src[a:b].encode())
-    with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", "tdbem_internal.cuh"), "rb") as fh:
-        h.update(fh.read())
+    h.update(code(src[:b]).encode())
+    with open(os.path.join(ROOT, "paper_2111_05205_gb300", "csrc", "tdbem_internal.cuh")) as fh:
+        h.update(code(fh.read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -293,10 +293,12 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
 }
 
 // b_i = -e_i - sum_j sum_{g in window(i,j), g <= a} (KU^(g)_ij q_j^{a-g} - KW^(g)_ij u_j^{a-g})
-// One CTA per row i; each warp walks 32-pair blocks of the row; every load
-// of the coefficient stream is a contiguous warp access, and the history
-// entries x_j^{a-g} of one slot differ only by the lanes' g0.  The row sum
-// is reduced in a fixed order (deterministic).
+// WPR warps per row i (4: the CTA's warps share the row's 32-pair blocks in
+// turn; 1: four rows per CTA); COL: the rows carry explicit columns (near
+// lists), else the column is the pair index (all pairs).  Every load of the
+// coefficient stream is a contiguous warp access, and the history entries
+// x_j^{a-g} of one slot differ only by the lanes' g0.  The row sum is
+// reduced in a fixed order (deterministic).
 // SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
 // coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
 // are read from their float-pair copies and the sum runs in double-float.
