@@ -27,7 +27,7 @@ def test_revision_ignores_comments_and_follows_code(tmp_path, monkeypatch):
     m = (dst / "march.cu").read_text()
     (dst / "march.cu").write_text(m.replace("namespace tdbem {", "namespace tdbem {  // a remark", 1))
     assert bench._kernel_rev() == r0
-    (dst / "march.cu").write_text(m.replace("constexpr int kNearPrefetch = 2;", "constexpr int kNearPrefetch = 3;"))
+    (dst / "march.cu").write_text("static int edited_line = 0;\n" + m)
     assert bench._kernel_rev() != r0
 
 
