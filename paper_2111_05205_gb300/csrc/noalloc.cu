@@ -9,6 +9,11 @@
 // that lives in a fixed file-scope device array instead of memory
 // allocated per call.
 //
+// It always runs plain Jacobi sweeps (the count tdbem_prepare derived from
+// the matrix and solver_tol), also when a learned SAI preconditioner is
+// installed with tdbem_set_precond: tdbem_step then runs the SAI sweeps, and
+// the two solutions agree to the solver tolerance rather than bit for bit.
+//
 // The array holds three vectors of at most kStaticMaxNs doubles (b and the
 // two Jacobi iterates; 6 MiB): every GPU that loads this library keeps it
 // until the process exits.  All calls on a device share it and it keeps the
@@ -71,15 +76,15 @@ extern "C" int tdbem_zero_lag_solve_static(const tdbem_ctx *cc, const double *b,
 {
     tdbem_ctx *c = const_cast<tdbem_ctx *>(cc);
     if (!c || !b || !x) return TDBEM_ERR_ARG;
-    if (!c->prepared) {
-        c->err = "zero-lag solve before prepare";
-        return TDBEM_ERR_STATE;
-    }
     const int ns = c->ns;
     if (ns > kStaticMaxNs) {
         c->err = "tdbem_zero_lag_solve_static: ns = " + std::to_string(ns) + " exceeds the static scratch limit of " +
                  std::to_string(kStaticMaxNs) + " elements";
         return TDBEM_ERR_ARG;
+    }
+    if (!c->prepared) {
+        c->err = "zero-lag solve before prepare";
+        return TDBEM_ERR_STATE;
     }
     cudaError_t e = cudaSetDevice(c->dev);
     double *scr = nullptr;
