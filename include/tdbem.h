@@ -76,7 +76,7 @@ typedef struct {
                              FP32 pipes; coefficients, the zero-lag matrix and the solve
                              are computed in FP64 either way */
     int32_t ps, pt;       /* FMM: interpolation points per space / time dimension (2..8,
-                             ps^3 pt <= 1024) */
+                             ps^3 pt <= 4096) */
     int32_t mu;           /* FMM: near-future intervals (Section 4.2); 0 = the smallest value
                              for which the kernel is a polynomial over every distant-future
                              interval (the paper uses 8) */
@@ -206,6 +206,22 @@ const char *tdbem_batch_last_error(const tdbem_batch *batch);
  * Synchronises the device. */
 int tdbem_grid_barrier_probe(int32_t nblocks, int32_t starve, int32_t *timed_out);
 
+/* Self-check of the split-precision tensor-core GEMM that evaluates the
+ * M2L contraction (Section 4.2, Eq. m2l_actual written as operator stack x
+ * moments; the paper gives no kernel).  Computes, on the current device,
+ *   c[j*m + i] = sum_{p < nprod} A_{s_p}[i, :] . B_{t_p}[j, :],
+ * s_p = prod[p] >> 4, t_p = prod[p] & 15, for i < m, j < n, where the terms
+ * A_s are a[(s*m + i)*k + x] (nta terms, 1..3) and B_t are b[(t*n + j)*k + x]
+ * (ntb terms, 1..3), all 16-bit floating-point numbers (fmt 1 = BF16, 0 =
+ * FP16) given as their bit patterns, with FP32 accumulation in tensor
+ * memory (tcgen05.mma, operands loaded by TMA; bn = 128 or 256 columns per
+ * tile).  Host buffers a[nta*m*k], b[ntb*n*k] (copied) and c[m*n] (FP32
+ * out).  ERR_ARG on a bad size or product; ERR_CUDA on a CUDA failure;
+ * ERR_TIMEOUT if a pipeline wait of the kernel gave up (every wait is
+ * bounded by about 2 s).  Synchronous.  For tests of the kernel only. */
+int tdbem_tc_gemm_check(int32_t m, int32_t n, int32_t k, int32_t nta, int32_t ntb, const int32_t *prod, int32_t nprod,
+                        int32_t fmt, int32_t bn, const uint16_t *a, const uint16_t *b, float *c);
+
 /* Learned sparse approximate inverse for the zero-lag solve (an addition
  * of this library; the paper only states that the system is sparse).  A
  * trainer holds a 2-layer network (5*width inputs -> hidden ReLU -> width
@@ -319,15 +335,17 @@ int tdbem_sync(tdbem_ctx *ctx);
  * point where they solve, e.g. code that runs while someone else captures a
  * CUDA graph, or hosts that forbid allocation after start-up).  Solves
  * A x = b with the context's zero-lag matrix (Eq. linear, built by
- * tdbem_prepare) by the same Jacobi sweeps tdbem_step uses, with its scratch
- * (b and two iterates) in a fixed file-scope device array of 3 x 262144
- * doubles (6 MiB) that every GPU loading the library keeps until exit.
- * b[ns] in, x[ns] out: host buffers (on_device = 0; the call returns after
- * the copy back) or device buffers (on_device = 1; asynchronous); b and x
- * must not overlap.  Work goes on the stream given to tdbem_create.
- * ERR_ARG if ns exceeds 262144.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current)
- * and should come before any stream capture.  All calls on one device share
+ * tdbem_prepare) by the Jacobi sweeps tdbem_step uses (always plain Jacobi:
+ * a learned SAI preconditioner installed by tdbem_set_precond is ignored, so
+ * then the two solutions agree to solver_tol, not bit for bit), with its
+ * scratch (b and two iterates) in a fixed file-scope device array of
+ * 3 x 262144 doubles (6 MiB) that every GPU loading the library keeps until
+ * exit.  b[ns] in, x[ns] out: host buffers (on_device = 0; the call returns
+ * after the copy back) or device buffers (on_device = 1; asynchronous); b
+ * and x must not overlap.  Work goes on the stream given to tdbem_create.
+ * ERR_ARG if ns exceeds 262144 (checked first, x untouched).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and should come before any stream capture.  All calls on one device share
  * the array and it keeps the last call's contents: calls that overlap on the
  * GPU race.  No cudaMalloc, cudaFree or allocating library call is made. */
 int tdbem_zero_lag_solve_static(const tdbem_ctx *ctx, const double *b, double *x, int32_t on_device);

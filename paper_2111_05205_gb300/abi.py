@@ -91,6 +91,7 @@ SIGNATURES = {
     "tdbem_sync": (ctypes.c_int, [_P]),
     "tdbem_zero_lag_solve_static": (ctypes.c_int, [_P, _P, _P, _I]),
     "tdbem_grid_barrier_probe": (ctypes.c_int, [_I, _I, ctypes.POINTER(_I)]),
+    "tdbem_tc_gemm_check": (ctypes.c_int, [_I, _I, _I, _I, _I, _P, _I, _I, _I, _P, _P, _P]),
 }
 
 _lib = None
@@ -373,3 +374,21 @@ def tdbem_grid_barrier_probe(nblocks, starve):
     if code != TDBEM_OK:
         raise TdbemError(code, "tdbem_grid_barrier_probe")
     return bool(out.value)
+
+
+def tdbem_tc_gemm_check(a, b, prod, fmt=1, bn=128):
+    """Run the tensor-core GEMM self-check: a [nta, m, k] and b [ntb, n, k]
+    uint16 bit patterns (BF16 if fmt = 1, FP16 if fmt = 0), prod a list of
+    (A term, B term); returns c [n, m] float32."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    b = np.ascontiguousarray(b, dtype=np.uint16)
+    nta, m, k = a.shape
+    ntb, n, k2 = b.shape
+    assert k == k2
+    pr = np.ascontiguousarray([(s << 4) | t for s, t in prod], dtype=np.int32)
+    c = np.zeros((n, m), dtype=np.float32)
+    code = lib().tdbem_tc_gemm_check(m, n, k, nta, ntb, _ptr(pr), len(pr), int(fmt), int(bn), _ptr(a), _ptr(b),
+                                     _ptr(c))
+    if code != TDBEM_OK:
+        raise TdbemError(code, "tdbem_tc_gemm_check")
+    return c

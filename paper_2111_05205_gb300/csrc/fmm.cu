@@ -700,8 +700,8 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     }
     F.P3 = F.ps * F.ps * F.ps;
     F.P = F.P3 * F.pt;
-    if (F.P > 1024) {
-        why = "FMM needs ps^3 pt <= 1024";
+    if (F.P > 4096) {
+        why = "FMM needs ps^3 pt <= 4096";
         return cudaSuccess;
     }
     double box[4];

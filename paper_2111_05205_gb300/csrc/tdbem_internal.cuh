@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libtdbem.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -103,6 +104,40 @@ struct Fmm {
     double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
     int far_k = -1;                         // leaf interval the far field belongs to
 };
+
+// Split-precision tensor-core GEMM (tc_gemm.cu): one output tile of at most
+// 128 rows (A rows) x BN columns (B rows), C[c_off + j ldc + i].
+constexpr int kTcBM = 128;
+constexpr int kTcBK = 64;          // K elements per 128-byte swizzle row
+constexpr int kTcMaxTerms = 3;
+constexpr int kTcMaxProd = 6;
+constexpr int kTcSmemBudget = 232448;  // dynamic shared memory per CTA (227 KB)
+
+struct TcTile {
+    int32_t a_row, b_row;  // first row of the tile in term 0 of A and B
+    int32_t rows, cols;    // valid rows (<= 128) and columns (<= BN)
+    int64_t c_off;         // C index of (row 0, column 0)
+};
+
+struct TcGemmArgs {
+    int32_t nta, ntb;                 // terms of A and B
+    int32_t a_term_rows, b_term_rows; // row distance between consecutive terms
+    int32_t nprod;
+    int32_t prod[kTcMaxProd];         // (A term << 4) | B term
+    int32_t kchunks;                  // K / 64
+    int32_t nstage;                   // shared-memory pipeline stages
+    int32_t fmt;                      // 0 = FP16, 1 = BF16
+    int64_t ldc;
+    float *C;
+    const TcTile *tiles;
+    int *err;                         // bit 1: a wait gave up
+};
+
+cudaError_t tc_make_map(CUtensorMap *map, const void *base, int64_t rows, int kp, int box_rows);
+int tc_stages(int nta, int ntb, int bn);
+size_t tc_smem_bytes(int nta, int ntb, int bn, int nstage);
+cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const TcGemmArgs &a, int ntiles, int bn,
+                           cudaStream_t s);
 
 struct Pending {
     int phase;
