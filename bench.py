@@ -353,7 +353,7 @@ def run_ours(args):
                                "m2l_ms_per_step": stf["ms_m2l"] / args.steps,
                                "near_ms_per_step": stf["ms_near"] / args.steps,
                                "far_ms_per_step": stf["ms_far"] / args.steps, "setup_s": round(fsetup, 2),
-                               "m2l_buckets_by_level": stf["m2l_buckets"][:args.depth + 1]}
+                               "m2l_tile_n_by_level": stf["m2l_tile_n"][:args.depth + 1]}
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, rows=args.cpu_rows)

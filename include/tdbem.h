@@ -107,9 +107,12 @@ typedef struct {
     int32_t fmm_lt, fmm_mu;        /* FMM: steps per leaf interval, near-future intervals */
     double ms_m2l;                 /* FMM: gather + M2L GEMMs + reduction, all levels */
     int64_t launches_m2l;          /* FMM: level M2L applications */
-    double m2l_flops;              /* FMM: 2 (mu+1+d) P^2 per interaction pair and application */
-    int32_t m2l_buckets[11];       /* FMM: batched-GEMM groups per level chosen by the setup-time
-                                      autotuner (0 for levels without interaction pairs) */
+    double m2l_flops;              /* FMM: algorithmic M2L flops, 2 P per operator row and pair and
+                                      application (rows of all-zero operator blocks not counted in
+                                      the tensor-core forms) */
+    int32_t m2l_tile_n[11];        /* FMM, tensor-core forms: GEMM tile width (columns) per level
+                                      chosen by the setup-time tuner (0 for levels without
+                                      interaction pairs or in the FP64 form) */
 } tdbem_stats;
 
 /* Creates a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -142,9 +145,13 @@ int tdbem_set_bc(tdbem_ctx *ctx, const int8_t *phi);
  * (the default).  ERR_ARG on a non-finite sample. */
 int tdbem_set_known(tdbem_ctx *ctx, const double *f);
 
-/* Incident plane pulse u_in(x,t) = f(t - t0 - k.x/c), f(s) = exp(-(s/width)^2)
- * (shape 0), k = dir normalised.  Replaces nothing else; without this call
- * there is no incident wave. */
+/* Incident plane pulse u_in(x,t) = f(t - t0 - k.x/c), k = dir normalised:
+ * shape 0, the Gaussian f(s) = exp(-(s/width)^2); shape 1, the raised cosine
+ * of Section 5.1.1 (Eq. uin), f(s) = 0.5 (1 - cos(2 pi c s / width)) for
+ * 0 <= c s <= width and 0 otherwise (width = the pulse length Lambda; with
+ * t0 = 0 and dir = +x_1 this is the paper's 0.5 (1 - Cos(2 pi (ct - x_1) /
+ * Lambda))).  Replaces nothing else; without this call there is no incident
+ * wave.  ERR_ARG for another shape, a zero direction or width <= 0. */
 int tdbem_set_incident_plane(tdbem_ctx *ctx, const double dir[3], double t0, double width, int32_t shape);
 
 /* Builds everything the marching needs on the device: element geometry,

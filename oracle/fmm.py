@@ -29,9 +29,12 @@ def n_aux(d):
 # - interpolation: Lagrange polynomials on the p Chebyshev points of the
 #   first kind, omega_a = cos((2a+1) pi / (2p)) (any cardinal interpolant
 #   fits Formula 1; the paper's cubic Hermite is not used);
-# - the interpolation box of a level-l cell is its cube (side s_l =
-#   side / 2^l) enlarged by rho = the largest centroid-to-vertex distance
-#   of any element: centre lo + (c + 1/2) s_l, half-width hs_l = s_l/2 + rho;
+# - interpolation boxes of a level-l cell (side s_l = side / 2^l, centre
+#   lo + (c + 1/2) s_l): as a source box its cube enlarged by rho = the
+#   largest centroid-to-vertex distance of any element, half-width hs_l =
+#   s_l/2 + rho, since an element reaches up to rho beyond the cell that
+#   holds its centroid; as an observation box the cube itself, half-width
+#   ho_l = s_l/2, since the observation points are the centroids;
 # - time: a leaf interval holds Lt = floor((s_L - rho) / (c dt)) steps, so
 #   that no source of an interval reaches an interaction-list target in the
 #   same interval; a level-l interval holds T_l = Lt 2^(L-l) steps.  Source
@@ -39,8 +42,8 @@ def n_aux(d):
 #   t_sigma), observation interval I_k covers steps alpha in [k T + 1,
 #   (k+1) T + 1); J_k has centre (k T + (T-1)/2) dt and half-length
 #   T dt / 2, I_k the same shifted by dt;
-# - mu: the smallest integer with c (mu T_l + 1) dt > sqrt(3) (3 s_l + 2
-#   hs_l) on every level, so that the kernel is an ordinary polynomial of
+# - mu: the smallest integer with c (mu T_l + 1) dt > sqrt(3) (3 s_l + hs_l
+#   + ho_l) on every level, so that the kernel is an ordinary polynomial of
 #   degree d over the node domain of I_{k+mu+1} x J_k (Section 4.2).
 
 
@@ -80,13 +83,14 @@ class Hierarchy:
         cdt = c * dt
         self.s = [self.side / (1 << l) for l in range(L + 1)]
         self.hs = [self.s[l] / 2.0 + self.rho for l in range(L + 1)]
+        self.ho = [self.s[l] / 2.0 for l in range(L + 1)]
         self.Lt = int(np.floor((self.s[L] - self.rho) / cdt))
         if self.Lt < 1 or not (2.0 * self.rho < self.s[L]):
             raise ValueError("infeasible hierarchy: leaf cells too small for c dt and the element size")
         self.Tl = [self.Lt * (1 << (L - l)) for l in range(L + 1)]
         m = 0
         for l in range(2, L + 1):
-            rmax = np.sqrt(3.0) * (3.0 * self.s[l] + 2.0 * self.hs[l])
+            rmax = np.sqrt(3.0) * (3.0 * self.s[l] + self.hs[l] + self.ho[l])
             m = max(m, int(np.floor((rmax / cdt - 1.0) / self.Tl[l])) + 1)
         self.mu = max(m, mu)
         self.ws, self.wt = cheb(ps), cheb(pt)
@@ -109,10 +113,12 @@ class Hierarchy:
         cen, h = self.src_interval(l, k)
         return cen + self.dt, h
 
-    def space_basis(self, l, ci, y):
-        """ell_b((y - centre)/hs) for b = (b1, b2, b3), b1 fastest, and its
-        gradient with respect to y ([P_s], [P_s, 3])."""
-        xi = (np.asarray(y) - self.centre(l, ci)) / self.hs[l]
+    def space_basis(self, l, ci, y, obs=False):
+        """ell_b((y - centre)/h) for b = (b1, b2, b3), b1 fastest, and its
+        gradient with respect to y ([P_s], [P_s, 3]); h = hs_l on the source
+        box, ho_l on the observation box (obs=True)."""
+        h = self.ho[l] if obs else self.hs[l]
+        xi = (np.asarray(y) - self.centre(l, ci)) / h
         vals, ders = zip(*(lagrange(self.ws, x) for x in xi))
         p = self.ps
         val = np.zeros(p ** 3)
@@ -122,9 +128,9 @@ class Hierarchy:
                 for b1 in range(p):
                     b = b1 + p * (b2 + p * b3)
                     val[b] = vals[0][b1] * vals[1][b2] * vals[2][b3]
-                    grad[b] = [ders[0][b1] * vals[1][b2] * vals[2][b3] / self.hs[l],
-                               vals[0][b1] * ders[1][b2] * vals[2][b3] / self.hs[l],
-                               vals[0][b1] * vals[1][b2] * ders[2][b3] / self.hs[l]]
+                    grad[b] = [ders[0][b1] * vals[1][b2] * vals[2][b3] / h,
+                               vals[0][b1] * ders[1][b2] * vals[2][b3] / h,
+                               vals[0][b1] * vals[1][b2] * ders[2][b3] / h]
         return val, grad
 
 
@@ -202,14 +208,15 @@ def kernel(x, y, t, s, c, d):
     return np.where(z > 0, np.maximum(z, 0.0) ** d, 0.0) / r[:, None, :, None]
 
 
-def node_points(H, l, ci):
+def node_points(H, l, ci, obs=False):
     p = H.ps
+    h = H.ho[l] if obs else H.hs[l]
     cen = H.centre(l, ci)
     pts = np.zeros((p ** 3, 3))
     for b3 in range(p):
         for b2 in range(p):
             for b1 in range(p):
-                pts[b1 + p * (b2 + p * b3)] = cen + H.hs[l] * np.array([H.ws[b1], H.ws[b2], H.ws[b3]])
+                pts[b1 + p * (b2 + p * b3)] = cen + h * np.array([H.ws[b1], H.ws[b2], H.ws[b3]])
     return pts
 
 
@@ -217,7 +224,7 @@ def m2l_naive(H, l, Ms, O, k):
     """L(O, I_k) = sum_{k' < k} sum_{S in IL(O)} U(O, S, I_k, J_k') M(S, J_k')
     (Eq. m2l_actual) with U sampled at the interpolation nodes (Eq. Uabmn);
     Ms[k'] are the level-l moments.  Returns [P_s, P_t]."""
-    xo = node_points(H, l, O)
+    xo = node_points(H, l, O, obs=True)
     ci, hi = H.obs_interval(l, k)
     to = ci + hi * H.wt
     Lloc = np.zeros((H.ps ** 3, H.pt))
@@ -236,7 +243,7 @@ def l2p(H, l, O, Lloc, i, alpha, bie):
     BMBIE applies (d/dn_x - c^-1 d/dt) to ell_a ell_m (Section 3)."""
     ci, hi = H.obs_interval(l, (alpha - 1) // H.Tl[l])
     lt, dlt = lagrange(H.wt, (alpha * H.dt - ci) / hi)
-    val, grad = H.space_basis(l, O, H.xc[i])
+    val, grad = H.space_basis(l, O, H.xc[i], obs=True)
     if bie == "obie":
         return float(val @ Lloc @ lt)
     dn = grad @ H.n[i]

@@ -42,16 +42,35 @@ def dgauss(t, sigma, t0):
     return -2.0 * s / sigma * np.exp(-s * s)
 
 
+def raised_cosine(t, length, c, t0):
+    """The pulse of Section 5.1.1 (Eq. uin) as a function of time at a fixed
+    point: 0.5 (1 - Cos(2 pi c (t - t0) / length)), where Cos is the cosine on
+    [0, 2 pi] and 1 elsewhere."""
+    x = 2.0 * np.pi * c * (np.asarray(t, dtype=np.float64) - t0) / length
+    return np.where((x >= 0.0) & (x <= 2.0 * np.pi), 0.5 * (1.0 - np.cos(x)), 0.0)
+
+
+def draised_cosine(t, length, c, t0):
+    x = 2.0 * np.pi * c * (np.asarray(t, dtype=np.float64) - t0) / length
+    return np.where((x >= 0.0) & (x <= 2.0 * np.pi), 0.5 * np.sin(x) * 2.0 * np.pi * c / length, 0.0)
+
+
 def incident_rhs(w, xc, n, alpha):
     """e_i(t_alpha): u_in (OBIE) or (d/dn_x - c^-1 d/dt) u_in (BMBIE) at the
-    collocation points, for the plane pulse u_in = g(t - t0 - k.x/c)."""
+    collocation points, for the plane pulse u_in = g(t - t0 - k.x/c), g the
+    Gaussian of width sigma (w.shape 0) or the raised cosine of length sigma
+    (w.shape 1)."""
     t = alpha * w.dt
     k = np.asarray(w.direction, dtype=np.float64)
     xi = t - (k @ xc.T) / w.c  # argument shifted by t0 inside g
+    if getattr(w, "shape", 0) == 1:
+        g, dg = raised_cosine(xi, w.sigma, w.c, w.t0), draised_cosine(xi, w.sigma, w.c, w.t0)
+    else:
+        g, dg = gauss(xi, w.sigma, w.t0), dgauss(xi, w.sigma, w.t0)
     if w.bie == "obie":
-        return gauss(xi, w.sigma, w.t0)
+        return g
     # d/dn_x g(t - t0 - k.x/c) = -(k.n / c) g';  c^-1 d/dt g = g' / c
-    return -(1.0 + n @ k) / w.c * dgauss(xi, w.sigma, w.t0)
+    return -(1.0 + n @ k) / w.c * dg
 
 
 def known_coefficients(w, nt):

@@ -41,11 +41,11 @@ class tdbem_stats(ctypes.Structure):
                 ("solve_contraction", ctypes.c_double), ("ms_prepare", ctypes.c_double),
                 ("ms_far", ctypes.c_double), ("launches_far", ctypes.c_int64), ("fmm_lt", ctypes.c_int32),
                 ("fmm_mu", ctypes.c_int32), ("ms_m2l", ctypes.c_double), ("launches_m2l", ctypes.c_int64),
-                ("m2l_flops", ctypes.c_double), ("m2l_buckets", ctypes.c_int32 * 11)]
+                ("m2l_flops", ctypes.c_double), ("m2l_tile_n", ctypes.c_int32 * 11)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["m2l_buckets"] = list(self.m2l_buckets)
+        d["m2l_tile_n"] = list(self.m2l_tile_n)
         return d
 
 

@@ -128,6 +128,7 @@ int check_flags(tdbem_ctx *c)
     int f = 0;
     TD_CUDA(cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f & 1) return fail(c, TDBEM_ERR_DIVERGED, "non-finite solution value (divergence guard)");
+    if (f & 8) return fail(c, TDBEM_ERR_TIMEOUT, "M2L tensor-core GEMM: a pipeline wait timed out");
     if (f & 4) {
         // a grid barrier of the fused solve gave up waiting: reset it and
         // solve with one launch per sweep from now on
@@ -148,12 +149,12 @@ int tdbem_create(const tdbem_params *p, void *stream, tdbem_ctx **out)
     if (!p || !out) return TDBEM_ERR_ARG;
     *out = nullptr;
     if (!(p->c > 0) || !(p->dt > 0) || p->nt < 2 || p->d < 1 || p->d > kMaxD || (p->bie != 0 && p->bie != 1) ||
-        (p->algo != 0 && p->algo != 1) || (p->precision != 0 && p->precision != 1))
+        (p->algo != 0 && p->algo != 1) || p->precision < 0 || p->precision > 3)
         return TDBEM_ERR_ARG;
     c = new tdbem_ctx();
     c->P = *p;
     c->cdt = p->c * p->dt;
-    c->split = (p->precision == 1);
+    c->split = (p->precision >= 1);
     c->user = (cudaStream_t)stream;
     cudaGetDevice(&c->dev);
     if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -249,13 +250,14 @@ int tdbem_set_known(tdbem_ctx *c, const double *f)
 int tdbem_set_incident_plane(tdbem_ctx *c, const double dir[3], double t0, double width, int32_t shape)
 {
     if (!c || !dir) return TDBEM_ERR_ARG;
-    if (shape != 0) return fail(c, TDBEM_ERR_ARG, "only the Gaussian pulse (shape 0) is implemented");
+    if (shape != 0 && shape != 1) return fail(c, TDBEM_ERR_ARG, "shape must be 0 (Gaussian) or 1 (raised cosine)");
     double l = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
     if (!(l > 0) || !(width > 0)) return fail(c, TDBEM_ERR_ARG, "bad direction or width");
     c->inc.on = 1;
     for (int k = 0; k < 3; ++k) c->inc.k[k] = dir[k] / l;
     c->inc.t0 = t0;
     c->inc.width = width;
+    c->inc.shape = shape;
     return TDBEM_OK;
 }
 
@@ -940,7 +942,7 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->ms_m2l = c->ms[PH_M2L];
     o->launches_m2l = c->launches[PH_M2L];
     o->m2l_flops = c->m2l_flops;
-    for (int l = 0; l < 11 && l < (int)c->fmm.lev.size(); ++l) o->m2l_buckets[l] = c->fmm.lev[l].np ? c->fmm.lev[l].nbk : 0;
+    for (int l = 0; l < 11 && l < (int)c->fmm.lev.size(); ++l) o->m2l_tile_n[l] = c->fmm.lev[l].np ? c->fmm.lev[l].tile_n : 0;
     o->launches_far = c->launches[PH_FAR];
     o->fmm_lt = c->fmm.Lt;
     o->fmm_mu = c->fmm.mu;

@@ -5,16 +5,20 @@
 // Readings (the paper defers the hierarchy to its earlier study):
 //   - Lagrange interpolation on the p Chebyshev points of the first kind,
 //     cos((2a+1) pi / (2p)), in each of x1..x3, y1..y3, t, s;
-//   - the box of a level-l cell is its cube enlarged by rho, the largest
-//     centroid-to-vertex distance of the mesh (half-width s_l/2 + rho);
+//   - source box of a level-l cell: its cube enlarged by rho, the largest
+//     centroid-to-vertex distance of the mesh (half-width s_l/2 + rho), as a
+//     source element reaches up to rho beyond the cell of its centroid;
+//     observation box: the cube itself (half-width s_l/2), as the
+//     observation points are the centroids, which lie in their cells;
 //   - a leaf interval holds Lt = floor((s_L - rho)/(c dt)) steps (no source
 //     of an interval reaches an interaction-list target in the same
 //     interval); level l holds T_l = Lt 2^(L-l) steps; source interval J_k
 //     covers sigma in [k T, (k+1) T), observation interval I_k covers steps
 //     alpha in [k T + 1, (k+1) T + 1);
-//   - mu: the smallest integer with c (mu T_l + 1) dt > sqrt(3)(3 s_l + 2 h_l)
-//     on every level, so that the kernel is a polynomial of degree d over the
-//     node domain of every distant-future interval (Section 4.2).
+//   - mu: the smallest integer with c (mu T_l + 1) dt > sqrt(3)(3 s_l + h_l + o_l)
+//     on every level (h_l, o_l the source and observation half-widths), so
+//     that the kernel is a polynomial of degree d over the node domain of
+//     every distant-future interval (Section 4.2).
 // Vector index of moments and locals: b1 + ps (b2 + ps (b3 + ps n)), as in
 // the matrix form of Eq. m2l.
 #include <math.h>
@@ -22,6 +26,7 @@
 #include <algorithm>
 
 #include <cublas_v2.h>
+#include <cuda_bf16.h>
 
 #include "tdbem_internal.cuh"
 
@@ -80,7 +85,7 @@ __global__ void k_rho(int ns, const double *__restrict__ xyz, const int32_t *__r
 // As[j][b] = int_E n_y . grad ell_b dS (collapsed Gauss-Legendre rule, exact
 // for the degree 3(ps-1) of ell_b on a flat triangle), and the L2P values
 // Dv[i][a] = ell_a(x_i), Dn[i][a] = n_x . grad ell_a(x_i).
-__global__ void k_element_weights(int ns, int ps, int L, const double *__restrict__ box, double s, double hs,
+__global__ void k_element_weights(int ns, int ps, int L, const double *__restrict__ box, double s, double hs, double ho,
                                   const double *__restrict__ xyz, const int32_t *__restrict__ tri,
                                   const double *__restrict__ xc, const double *__restrict__ nrm,
                                   const uint64_t *__restrict__ key, int nq, const double *__restrict__ qx,
@@ -116,12 +121,12 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
         }
         At[(int64_t)j * P3 + b] = at;
         As[(int64_t)j * P3 + b] = as;
-        // L2P values at the collocation point of element j
+        // L2P values at the collocation point of element j (observation box)
         double l[3][kMaxP], dl[3][kMaxP];
-        for (int k = 0; k < 3; ++k) lag_basis(ps, (xc[3 * j + k] - cen[k]) / hs, l[k], dl[k]);
+        for (int k = 0; k < 3; ++k) lag_basis(ps, (xc[3 * j + k] - cen[k]) / ho, l[k], dl[k]);
         Dv[(int64_t)j * P3 + b] = l[0][b1] * l[1][b2] * l[2][b3];
         Dn[(int64_t)j * P3 + b] = (dl[0][b1] * l[1][b2] * l[2][b3] * n[0] + l[0][b1] * dl[1][b2] * l[2][b3] * n[1] +
-                                  l[0][b1] * l[1][b2] * dl[2][b3] * n[2]) / hs;
+                                  l[0][b1] * l[1][b2] * dl[2][b3] * n[2]) / ho;
     }
 }
 
@@ -132,8 +137,8 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
 // row = a + P3 m, col = b + P3 n:
 //   U(x_a, y_b, t_m, s_n) = (c (t_m - s_n) - r)_+^d / r,
 //   U^(p) = C(d, p) (c (t_m - s_n) - r)_+^(d-p) / r,
-// x_a - y_b = -offset s + h (w_a - w_b), t_m - s_n = l T dt + dt + ht (w_m - w_n).
-__global__ void k_m2l_operators(int ps, int pt, int d, int mu, double s, double hs, double T_dt, double dt,
+// x_a - y_b = -offset s + ho w_a - hs w_b, t_m - s_n = l T dt + dt + ht (w_m - w_n).
+__global__ void k_m2l_operators(int ps, int pt, int d, int mu, double s, double hs, double ho, double T_dt, double dt,
                                 double ht, double c, int noff, const int32_t *__restrict__ offs, double *op)
 {
     const int P3 = ps * ps * ps, P = P3 * pt, nblk = mu + 1 + d;
@@ -154,9 +159,9 @@ __global__ void k_m2l_operators(int ps, int pt, int d, int mu, double s, double 
         int a = row % P3, m = row / P3, b = col % P3, n = col / P3;
         int a1 = a % ps, a2 = (a / ps) % ps, a3 = a / (ps * ps);
         int b1 = b % ps, b2 = (b / ps) % ps, b3 = b / (ps * ps);
-        double rx = -dx * s + hs * (cheb_node(ps, a1) - cheb_node(ps, b1));
-        double ry = -dy * s + hs * (cheb_node(ps, a2) - cheb_node(ps, b2));
-        double rz = -dz * s + hs * (cheb_node(ps, a3) - cheb_node(ps, b3));
+        double rx = -dx * s + ho * cheb_node(ps, a1) - hs * cheb_node(ps, b1);
+        double ry = -dy * s + ho * cheb_node(ps, a2) - hs * cheb_node(ps, b2);
+        double rz = -dz * s + ho * cheb_node(ps, a3) - hs * cheb_node(ps, b3);
         double r = sqrt(rx * rx + ry * ry + rz * rz);
         int l = (blk <= mu) ? blk + 1 : mu + 1;
         int pw = (blk <= mu) ? 0 : blk - mu;
@@ -404,26 +409,80 @@ __global__ void k_l2p(int ns, int P3, int pt, int Lt, int bie, double c, const i
 
 namespace tdbem {
 
-// M2L as dense GEMMs grouped by cell offset: the moments of the source
-// cells of every interaction pair, ordered by (offset, observation cell),
-// are gathered into the columns of B; for each offset one GEMM multiplies
-// the offset's operator stack [(mu+1+d) P x P] with its slice of B; the
-// per-cell sums over the cell's pairs (fixed order) feed the locals.
-template <typename TB>
-__global__ void k_m2l_gather(int64_t np, int P, const int32_t *__restrict__ pS, const int64_t *__restrict__ pcol,
-                             const double *__restrict__ M, TB *B)
+// M2L as dense GEMMs grouped by symmetry class of the cell offset.  Column
+// j of a class's GEMM is one interaction pair (O, S) whose offset is g(c):
+// it holds the source moment with its spatial node index permuted by g,
+// B_j[b + P3 n] = M_S[g(b) + P3 n], so that the class's canonical operator
+// stack applies; row a + P3 m + P blk of the product then belongs to node
+// g(a) of O's local (a reduction reads it back through g^-1).
+__global__ void k_m2l_gather(int64_t np, int P3, int P, const int32_t *__restrict__ pS, const uint8_t *__restrict__ pg,
+                             const int16_t *__restrict__ perm, const double *__restrict__ M, double *B)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * P; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t pr = e / P;
-        int r = (int)(e % P);
-        B[pcol[pr] * P + r] = (TB)M[(int64_t)pS[pr] * P + r];
+        const int64_t col = e / P;
+        const int r = (int)(e % P), b = r % P3;
+        B[e] = M[(int64_t)pS[col] * P + perm[pg[col] * P3 + b] + (r - b)];
     }
 }
 
-__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *b)
+// Terms of the split of x into nterm BF16 numbers, x ~ t_0 + t_1 + ..,
+// t_k = bf16(x - t_0 - .. - t_{k-1}) (round to nearest), as bit patterns.
+__device__ __forceinline__ void split_bf16(double x, int nterm, uint16_t *t)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        b[e] = (float)a[e];
+    for (int k = 0; k < nterm; ++k) {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        t[k] = __bfloat16_as_ushort(h);
+        x -= (double)__bfloat162float(h);
+    }
+}
+
+// Gather with the split: Bt[k][col][r] for r < P (the columns' padding to Kp
+// stays zero).
+__global__ void k_m2l_gather_split(int64_t np, int P3, int P, int Kp, int nterm, const int32_t *__restrict__ pS,
+                                   const uint8_t *__restrict__ pg, const int16_t *__restrict__ perm,
+                                   const double *__restrict__ M, uint16_t *Bt)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * P; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = e / P;
+        const int r = (int)(e % P), b = r % P3;
+        uint16_t t[kTcMaxTerms];
+        split_bf16(M[(int64_t)pS[col] * P + perm[pg[col] * P3 + b] + (r - b)], nterm, t);
+        for (int k = 0; k < nterm; ++k) Bt[((int64_t)k * np + col) * Kp + r] = t[k];
+    }
+}
+
+// Operator terms: opt[k][c][row][col] (row < R, col < P) from the FP64
+// stacks op[c][row][col]; padding rows and columns stay zero.
+__global__ void k_split_operators(int ncls, int R, int P, int Rp, int Kp, int nterm, const double *__restrict__ op,
+                                  uint16_t *opt)
+{
+    const int64_t n = (int64_t)ncls * R * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int col = (int)(e % P);
+        const int64_t cr = e / P;
+        const int row = (int)(cr % R), c = (int)(cr / R);
+        uint16_t t[kTcMaxTerms];
+        split_bf16(op[e], nterm, t);
+        for (int k = 0; k < nterm; ++k) opt[(((int64_t)k * ncls + c) * Rp + row) * Kp + col] = t[k];
+    }
+}
+
+// Largest |entry| of each (class, block) of the FP64 operator stacks, for
+// skipping GEMM tiles whose rows are all zero (blocks before the wavefront
+// reaches the node domain).  One CTA per (class, block).
+__global__ void k_block_maxabs(int P, int nblk, const double *__restrict__ op, double *out)
+{
+    __shared__ double red[256];
+    const double *q = op + (int64_t)blockIdx.x * P * P;
+    double m = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)P * P; e += blockDim.x) m = fmax(m, fabs(q[e]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
 // Exact sum of two floats (two-sum of Knuth): a + b = s + e.
@@ -435,61 +494,52 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
     hi = s;
 }
 
+// Per observation cell O (one CTA): every row e = a' + P3 m + P blk of O's
+// locals summed over O's pairs in interaction-list order, pair t's product
+// read at row g_t^-1(a') + P3 m + P blk.  FP32 products are summed in
+// double-float (a float pair updated by two-sums, about 48 bits): the far
+// field cancels terms 1e4-1e5 larger than itself, so a plain FP32 sum is not
+// enough, and FP64 adds are 57 times slower than FP32 ones on this GPU.
+// Near-future rows go to the ring of locals, derivative rows to G.
 template <typename TC>
-__global__ void k_m2l_reduce(int nc, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
-                             const int64_t *__restrict__ oidx, const TC *__restrict__ C, double *ring, double *G)
+__global__ void k_m2l_reduce(int nc, int P3, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
+                             const int64_t *__restrict__ oidx, const uint8_t *__restrict__ og,
+                             const int16_t *__restrict__ iperm, const TC *__restrict__ C, double *ring, double *G)
 {
-    // The cell's column indices are staged in shared memory (an interaction
-    // list holds at most 189 cells), so the operand loads do not wait on
-    // index loads.  Each thread sums 4 consecutive entries (one 16-byte load
-    // per column when R = nblk P is a multiple of 4) over the cell's columns
-    // in list order, 8 columns' loads at a time.  FP32 columns are summed in
-    // double-float (a float pair with two-sum updates, about 48 bits): the
-    // far field cancels terms 1e4-1e5 larger than itself, so a plain FP32
-    // sum is not enough, and FP64 adds are 57 times slower on this GPU.
     __shared__ int64_t cols[kMaxIL];
+    __shared__ int32_t gofs[kMaxIL];
     const int R = nblk * P;
     const int O = blockIdx.x;
     const int64_t t0 = ooff[O];
     const int nt = (int)(ooff[O + 1] - t0);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) cols[t] = oidx[t0 + t] * R;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        cols[t] = oidx[t0 + t] * R;
+        gofs[t] = og[t0 + t] * P3;
+    }
     __syncthreads();
-    for (int e0 = 4 * threadIdx.x; e0 < R; e0 += 4 * blockDim.x) {
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
-        if ((R & 3) == 0 && sizeof(TC) == 4) {
-            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int e = threadIdx.x; e < R; e += blockDim.x) {
+        const int a = e % P3, rest = e - a;
+        double s = 0.0;
+        if (sizeof(TC) == 4) {
+            float hi = 0.f, lo = 0.f;
             int t = 0;
             for (; t + 8 <= nt; t += 8) {
-                float4 f[8];
+                float f[8];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) f[v] = *reinterpret_cast<const float4 *>(C + cols[t + v] + e0);
+                for (int v = 0; v < 8; ++v) f[v] = (float)C[cols[t + v] + iperm[gofs[t + v] + a] + rest];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    two_sum_acc(hi[0], lo[0], f[v].x);
-                    two_sum_acc(hi[1], lo[1], f[v].y);
-                    two_sum_acc(hi[2], lo[2], f[v].z);
-                    two_sum_acc(hi[3], lo[3], f[v].w);
-                }
+                for (int v = 0; v < 8; ++v) two_sum_acc(hi, lo, f[v]);
             }
-            for (; t < nt; ++t) {
-                const float4 f = *reinterpret_cast<const float4 *>(C + cols[t] + e0);
-                two_sum_acc(hi[0], lo[0], f.x);
-                two_sum_acc(hi[1], lo[1], f.y);
-                two_sum_acc(hi[2], lo[2], f.z);
-                two_sum_acc(hi[3], lo[3], f.w);
-            }
-            for (int q = 0; q < 4; ++q) s[q] = (double)hi[q] + (double)lo[q];
+            for (; t < nt; ++t) two_sum_acc(hi, lo, (float)C[cols[t] + iperm[gofs[t] + a] + rest]);
+            s = (double)hi + (double)lo;
         } else {
-            for (int q = 0; q < 4 && e0 + q < R; ++q)
-                for (int t = 0; t < nt; ++t) s[q] += (double)C[cols[t] + e0 + q];
+            for (int t = 0; t < nt; ++t) s += (double)C[cols[t] + iperm[gofs[t] + a] + rest];
         }
-        for (int q = 0; q < 4 && e0 + q < R; ++q) {
-            const int e = e0 + q, blk = e / P, r = e % P;
-            if (blk <= mu)
-                ring[((int64_t)((k + blk + 1) % nslot) * nc + O) * P + r] += s[q];
-            else
-                G[((int64_t)(blk - mu - 1) * nc + O) * P + r] = s[q];
-        }
+        const int blk = e / P, r = e % P;
+        if (blk <= mu)
+            ring[((int64_t)((k + blk + 1) % nslot) * nc + O) * P + r] += s;
+        else
+            G[((int64_t)(blk - mu - 1) * nc + O) * P + r] = s;
     }
 }
 
@@ -572,116 +622,163 @@ void cmp_table(int d, int k, double *out)
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-// Groups the level's offsets (in pair-count order) into nbk buckets of equal
-// offset count; each offset owns a slab of its bucket's largest pair count.
-static void m2l_layout(FmmLevel &V, int nbk)
+// Symmetries of the cube: g = 8 pi + sigma acts on vectors as
+// (g v)_k = s_k v_{pi(k)}, pi the permutation kPerm[pi] of the axes and s_k =
+// -1 where bit k of sigma is set.  On a node multi-index of p Chebyshev
+// points per axis (w_{p-1-i} = -w_i) it acts as (g b)_k = b_{pi(k)}, or
+// p - 1 - b_{pi(k)} where s_k = -1.
+static const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+static int sym_node(int p, int g, int b)
 {
-    nbk = std::max(1, std::min<int>(nbk, (int)V.ord.size()));
-    V.colbase.assign(343, 0);
-    V.buckets.clear();
-    int64_t col = 0;
-    for (int bk = 0; bk < nbk; ++bk) {
-        size_t lo = V.ord.size() * bk / nbk, hi = V.ord.size() * (bk + 1) / nbk;
-        if (hi <= lo) continue;
-        FmmBucket B;
-        B.first = (int)lo;
-        B.count = (int)(hi - lo);
-        B.n = V.ostart[V.ord[lo] + 1] - V.ostart[V.ord[lo]];
-        for (size_t t = lo; t < hi; ++t) {
-            V.colbase[V.ord[t]] = col;
-            col += B.n;
-        }
-        V.buckets.push_back(B);
-    }
-    V.ncol = std::max<int64_t>(col, 1);
-    V.nbk = nbk;
+    const int *pi = kPerm[g >> 3];
+    const int bb[3] = {b % p, (b / p) % p, b / (p * p)};
+    int out[3];
+    for (int k = 0; k < 3; ++k) out[k] = ((g >> k) & 1) ? p - 1 - bb[pi[k]] : bb[pi[k]];
+    return out[0] + p * (out[1] + p * out[2]);
 }
 
-// The batched GEMMs of one M2L application (operator stacks x gathered moments).
-static cublasStatus_t m2l_gemms(tdbem_ctx *c, FmmLevel &V)
+// o = g(c) with c the canonical offset (|c_0| >= |c_1| >= |c_2| >= 0, ties in
+// axis order); returns g.
+static int sym_decompose(const int o[3], int c[3])
+{
+    int idx[3] = {0, 1, 2};
+    std::stable_sort(idx, idx + 3, [&](int x, int y) { return abs(o[x]) > abs(o[y]); });
+    int pi[3];
+    for (int r = 0; r < 3; ++r) {
+        c[r] = abs(o[idx[r]]);
+        pi[idx[r]] = r;
+    }
+    int pidx = 0;
+    while (!(kPerm[pidx][0] == pi[0] && kPerm[pidx][1] == pi[1] && kPerm[pidx][2] == pi[2])) ++pidx;
+    int sigma = 0;
+    for (int k = 0; k < 3; ++k)
+        if (o[k] < 0) sigma |= 1 << k;
+    return 8 * pidx + sigma;
+}
+
+// GEMM tiles of one level for tile width bn: per class, the 128-row blocks
+// of its operator stack that are not all zero (bm: largest |entry| of every
+// (class, stack block)), times its columns in chunks of bn; *flops = the
+// algorithmic flops of the tiles kept.
+static std::vector<TcTile> m2l_tiles(const Fmm &F, const FmmLevel &V, int bn, const std::vector<double> &bm,
+                                     double *flops)
+{
+    std::vector<TcTile> t;
+    double fl = 0.0;
+    for (int ci = 0; ci < V.ncls; ++ci) {
+        const int64_t n = V.cbase[ci + 1] - V.cbase[ci];
+        if (n == 0) continue;
+        for (int r0 = 0; r0 < F.R; r0 += kTcBM) {
+            const int r1 = std::min(F.R, r0 + kTcBM);
+            bool zero = true;
+            for (int blk = r0 / F.P; blk <= (r1 - 1) / F.P; ++blk)
+                if (bm[(size_t)ci * F.nblk + blk] != 0.0) zero = false;
+            if (zero) continue;  // these rows of the products stay zero
+            fl += 2.0 * (r1 - r0) * F.P * (double)n;
+            for (int64_t j0 = 0; j0 < n; j0 += bn)
+                t.push_back({ci * F.Rp + r0, (int32_t)(V.cbase[ci] + j0), r1 - r0, (int32_t)std::min<int64_t>(bn, n - j0),
+                             (V.cbase[ci] + j0) * (int64_t)F.R + r0});
+        }
+    }
+    *flops = fl;
+    return t;
+}
+
+static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V)
+{
+    const Fmm &F = c->fmm;
+    TcGemmArgs g{};
+    g.nta = F.nta;
+    g.ntb = F.ntb;
+    g.a_term_rows = V.ncls * F.Rp;
+    g.b_term_rows = (int32_t)V.np;
+    g.nprod = F.nprod;
+    for (int p = 0; p < F.nprod; ++p) g.prod[p] = F.prod[p];
+    g.kchunks = F.Kp / kTcBK;
+    g.nstage = tc_stages(F.nta, F.ntb, V.tile_n);
+    g.fmt = 1;
+    g.ldc = F.R;
+    g.C = V.C32;
+    g.tiles = V.tiles;
+    g.err = c->d_flag;
+    return g;
+}
+
+// The products of one M2L application: every class's canonical operator
+// stack times its gathered columns.
+static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V)
 {
     Fmm &F = c->fmm;
-    const int P = F.P, R = F.nblk * P;
-    const long long sA = (long long)R * P;
-    cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
-    for (const FmmBucket &B : V.buckets) {
-        if (st != CUBLAS_STATUS_SUCCESS) break;
-        int64_t cb = V.colbase[V.ord[B.first]];
-        if (c->split) {
-            const float one = 1.0f, zero = 0.0f;
-            st = cublasGemmStridedBatchedEx(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one,
-                                            V.op32 + (size_t)B.first * sA, CUDA_R_32F, P, sA,
-                                            V.Bbuf32 + (size_t)cb * P, CUDA_R_32F, P, (long long)B.n * P, &zero,
-                                            V.Cbuf32 + (size_t)cb * R, CUDA_R_32F, R, (long long)B.n * R, B.count,
-                                            CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
-        } else {
-            const double one = 1.0, zero = 0.0;
-            st = cublasDgemmStridedBatched(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)B.n, P, &one,
-                                           V.op + (size_t)B.first * sA, P, sA, V.Bbuf + (size_t)cb * P, P,
-                                           (long long)B.n * P, &zero, V.Cbuf + (size_t)cb * R, R, (long long)B.n * R,
-                                           B.count);
+    if (c->split) return tc_gemm_launch(V.mapA, V.mapB, m2l_args(c, V), V.ntiles, V.tile_n, c->s);
+    const double one = 1.0, zero = 0.0;
+    for (int ci = 0; ci < V.ncls; ++ci) {
+        const int64_t c0 = V.cbase[ci], n = V.cbase[ci + 1] - c0;
+        if (n == 0) continue;
+        cublasStatus_t st = cublasDgemm(F.blas, CUBLAS_OP_T, CUBLAS_OP_N, F.R, (int)n, F.P, &one,
+                                        V.op + (size_t)ci * F.R * F.P, F.P, V.Bbuf + (size_t)c0 * F.P, F.P, &zero,
+                                        V.Cbuf + (size_t)c0 * F.R, F.R);
+        if (st != CUBLAS_STATUS_SUCCESS) {
+            c->err = "cuBLAS status " + std::to_string((int)st) + " in the FP64 M2L GEMM";
+            return cudaErrorUnknown;
         }
     }
-    return st;
+    return cudaSuccess;
 }
 
-// Autotuner: times the level's M2L GEMMs for 1, 2, 4, .. 32 buckets on the
-// real operators and shapes, keeps the fastest, and uploads the pair
-// columns of that layout.
-static cudaError_t m2l_tune_and_finalize(tdbem_ctx *c, FmmLevel &V)
+// Tile-width tuner of the tensor-core M2L (the level's classes, column
+// counts and zero blocks are fixed): times the level's GEMM with 128- and
+// 256-column tiles on its real operators, keeps the faster and uploads its
+// tile list and the moments' tensor map.
+static cudaError_t m2l_tune(tdbem_ctx *c, FmmLevel &V, const std::vector<double> &bm)
 {
+    Fmm &F = c->fmm;
     cudaStream_t s = c->s;
+    double fl = 0.0;
+    std::vector<TcTile> t128 = m2l_tiles(F, V, 128, bm, &fl);
+    F_TRY(falloc(c, &V.tiles, std::max<size_t>(t128.size(), 1)));
     cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    int best = 1;
+    F_TRY(cudaEventCreate(&e0));
+    F_TRY(cudaEventCreate(&e1));
+    int best = 128;
     float best_ms = 1e30f;
     V.tune.clear();
-    for (int nbk = 1; nbk <= 32; nbk *= 2) {
-        if (nbk > 1 && nbk > (int)V.ord.size()) break;
-        m2l_layout(V, nbk);
-        if (m2l_gemms(c, V) != CUBLAS_STATUS_SUCCESS) continue;  // warm-up; skip layouts the library rejects
+    cudaError_t err = cudaSuccess;
+    for (int bn : {128, 256}) {
+        std::vector<TcTile> t = bn == 128 ? t128 : m2l_tiles(F, V, bn, bm, &fl);
+        if ((err = cudaMemcpyAsync(V.tiles, t.data(), t.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            break;
+        if ((err = tc_make_map(&V.mapB, V.Bt, (int64_t)F.ntb * V.np, F.Kp, bn)) != cudaSuccess) break;
+        V.tile_n = bn;
+        V.ntiles = (int)t.size();
+        if ((err = m2l_products(c, V)) != cudaSuccess) break;  // warm-up
         cudaEventRecord(e0, s);
-        cublasStatus_t st = m2l_gemms(c, V);
+        err = m2l_products(c, V);
         cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (st != CUBLAS_STATUS_SUCCESS) continue;
-        V.tune.push_back({nbk, ms});
+        V.tune.push_back({bn, ms});
         if (ms < best_ms) {
             best_ms = ms;
-            best = nbk;
+            best = bn;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best_ms >= 1e30f) return cudaErrorUnknown;
-    m2l_layout(V, best);
-    std::vector<int64_t> pcol(V.np);
-    for (int o = 0; o < 343; ++o)
-        for (int64_t t = V.ostart[o]; t < V.ostart[o + 1]; ++t) pcol[t] = V.colbase[o] + (t - V.ostart[o]);
-    std::vector<int64_t> ooff(V.nc + 1, 0);
-    for (int32_t O : V.hpO) ooff[O + 1]++;
-    for (int O = 0; O < V.nc; ++O) {
-        if (ooff[O + 1] > kMaxIL) return cudaErrorInvalidValue;  // the reduction stages one list in shared memory
-        ooff[O + 1] += ooff[O];
-    }
-    std::vector<int64_t> oidx(V.np), fill(ooff.begin(), ooff.end() - 1);
-    for (int64_t t = 0; t < V.np; ++t) oidx[fill[V.hpO[t]]++] = pcol[t];
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(V.pS, V.hpS.data(), V.np * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return e;
-    if ((e = cudaMemcpyAsync(V.pcol, pcol.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return e;
-    if ((e = cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaMemcpyAsync(V.oidx, oidx.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return e;
-    V.hpO.clear();
-    V.hpS.clear();
-    return cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return err;
+    std::vector<TcTile> t = m2l_tiles(F, V, best, bm, &fl);
+    F_TRY(cudaMemcpyAsync(V.tiles, t.data(), t.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
+    F_TRY(tc_make_map(&V.mapB, V.Bt, (int64_t)F.ntb * V.np, F.Kp, best));
+    V.tile_n = best;
+    V.ntiles = (int)t.size();
+    V.flops_app = fl;
+    int flag = 0;
+    F_TRY(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    F_TRY(cudaStreamSynchronize(s));
+    return (flag & 8) ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 
 // Hierarchy parameters, per-element P2M/L2P tables, transfer matrices and
@@ -720,6 +817,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     for (int l = 0; l <= L; ++l) {
         F.lev[l].s = box[3] / (double)(1 << l);
         F.lev[l].hs = F.lev[l].s / 2.0 + F.rho;
+        F.lev[l].ho = F.lev[l].s / 2.0;
     }
     F.Lt = (int)floor((F.lev[L].s - F.rho) / cdt);
     if (F.Lt < 1 || !(2.0 * F.rho < F.lev[L].s)) {
@@ -729,7 +827,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     int mu = 0;
     for (int l = 2; l <= L; ++l) {
         F.lev[l].T = F.Lt << (L - l);
-        double rmax = sqrt(3.0) * (3.0 * F.lev[l].s + 2.0 * F.lev[l].hs);
+        double rmax = sqrt(3.0) * (3.0 * F.lev[l].s + F.lev[l].hs + F.lev[l].ho);
         mu = std::max(mu, (int)floor((rmax / cdt - 1.0) / F.lev[l].T) + 1);
     }
     F.lev[L].T = F.Lt;
@@ -738,15 +836,37 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     F.nd = d * (d - 1) / 2;
     F.nslot = F.mu + 2;
     const int P = F.P, P3 = F.P3, ps = F.ps, pt = F.pt;
-    if (cublasCreate(&F.blas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    cublasSetStream(F.blas, c->s);
-    cublasSetMathMode(F.blas, CUBLAS_DEFAULT_MATH);
-    if (c->split) {
-        cublasSetEmulationStrategy(F.blas, CUBLAS_EMULATION_STRATEGY_EAGER);
-        // moments and operators are finite: the unknowns are checked every
-        // step (a non-finite value stops the march), so the emulation need
-        // not scan its operands for infinities and NaNs
-        cublasSetEmulationSpecialValuesSupport(F.blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
+    F.R = F.nblk * P;
+    F.Rp = (F.R + kTcBM - 1) / kTcBM * kTcBM;
+    F.Kp = (P + kTcBK - 1) / kTcBK * kTcBK;
+    if (!c->split) {
+        // FP64 form: the products are FP64 GEMMs of the library
+        if (cublasCreate(&F.blas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        cublasSetStream(F.blas, c->s);
+        cublasSetMathMode(F.blas, CUBLAS_DEFAULT_MATH);
+    } else {
+        // tensor-core forms: BF16 terms of operators and moments, and the
+        // products (A term, B term) kept: all with s + t < nterm
+        const int nterm = c->P.precision == 1 ? 3 : c->P.precision == 2 ? 2 : 1;
+        F.nta = F.ntb = nterm;
+        F.nprod = 0;
+        for (int sum = 0; sum < nterm; ++sum)
+            for (int a = 0; a <= sum; ++a) F.prod[F.nprod++] = (a << 4) | (sum - a);
+    }
+    // node permutations of the 48 symmetries of the cube
+    {
+        std::vector<int16_t> pm(48 * P3), ip(48 * P3);
+        for (int g = 0; g < 48; ++g)
+            for (int b = 0; b < P3; ++b) {
+                const int gb = sym_node(ps, g, b);
+                pm[g * P3 + b] = (int16_t)gb;
+                ip[g * P3 + gb] = (int16_t)b;
+            }
+        F_TRY(falloc(c, &F.perm, pm.size()));
+        F_TRY(falloc(c, &F.iperm, ip.size()));
+        F_TRY(cudaMemcpyAsync(F.perm, pm.data(), pm.size() * sizeof(int16_t), cudaMemcpyHostToDevice, c->s));
+        F_TRY(cudaMemcpyAsync(F.iperm, ip.data(), ip.size() * sizeof(int16_t), cudaMemcpyHostToDevice, c->s));
+        F_TRY(cudaStreamSynchronize(c->s));
     }
 
     // per-element tables (leaf boxes)
@@ -762,7 +882,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     F_TRY(falloc(c, &d_qw, nq));
     F_TRY(cudaMemcpyAsync(d_qx, qx.data(), nq * sizeof(double), cudaMemcpyHostToDevice, c->s));
     F_TRY(cudaMemcpyAsync(d_qw, qw.data(), nq * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    k_element_weights<<<ns, 128, 0, c->s>>>(ns, ps, L, c->tree.box, F.lev[L].s, F.lev[L].hs, c->d_xyz, c->d_tri,
+    k_element_weights<<<ns, 128, 0, c->s>>>(ns, ps, L, c->tree.box, F.lev[L].s, F.lev[L].hs, F.lev[L].ho, c->d_xyz, c->d_tri,
                                            c->d_xc, c->d_n, c->tree.key, nq, d_qx, d_qw, F.At, F.As, F.Dv, F.Dn);
     F_TRY(cudaGetLastError());
 
@@ -813,20 +933,28 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         F_TRY(falloc(c, &V.D, (size_t)std::max(d, 1) * V.nc * P));
         F_TRY(falloc(c, &V.A, (size_t)std::max(F.nd, 1) * V.nc * P));
         F_TRY(falloc(c, &V.G, (size_t)std::max(d, 1) * V.nc * P));
-        // spatial transfer from this level (child) to level l-1 (parent):
-        // S[pos][b'][b] = ell_b'(((pos - 1/2) s_l + h_l w_b) / h_{l-1})
+        // spatial transfers between this level (child) and level l-1
+        // (parent): S[pos][b'][b] = ell_b'(((pos - 1/2) s_l + h_l w_b) / h_{l-1})
+        // on the source boxes (M2M) and on the observation boxes (L2L)
         if (l > 2) {
-            std::vector<double> sm(2 * ps * ps);
-            for (int pos = 0; pos < 2; ++pos)
-                for (int b = 0; b < ps; ++b) {
-                    double v[kMaxP];
-                    h_lagrange(ps, ((pos - 0.5) * V.s + V.hs * h_cheb(ps, b)) / F.lev[l - 1].hs, v, nullptr);
-                    for (int bp = 0; bp < ps; ++bp) sm[pos * ps * ps + bp * ps + b] = v[bp];
-                }
-            F_TRY(falloc(c, &V.Sm, sm.size()));
-            F_TRY(cudaMemcpyAsync(V.Sm, sm.data(), sm.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+            for (int kind = 0; kind < 2; ++kind) {
+                const double hc = kind ? V.ho : V.hs, hp = kind ? F.lev[l - 1].ho : F.lev[l - 1].hs;
+                std::vector<double> sm(2 * ps * ps);
+                for (int pos = 0; pos < 2; ++pos)
+                    for (int b = 0; b < ps; ++b) {
+                        double v[kMaxP];
+                        h_lagrange(ps, ((pos - 0.5) * V.s + hc * h_cheb(ps, b)) / hp, v, nullptr);
+                        for (int bp = 0; bp < ps; ++bp) sm[pos * ps * ps + bp * ps + b] = v[bp];
+                    }
+                double **dst = kind ? &V.So : &V.Sm;
+                F_TRY(falloc(c, dst, sm.size()));
+                F_TRY(cudaMemcpyAsync(*dst, sm.data(), sm.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+            }
         }
-        // interaction pairs grouped by offset, and per observation cell
+        // interaction pairs as GEMM columns, grouped by the symmetry class of
+        // their offset (classes by canonical offset code, pairs by observation
+        // cell and list position), and per observation cell in list order
+        std::vector<int32_t> codes;  // canonical offset of each class
         {
             const TreeLevel &T = c->tree.levels[l];
             std::vector<int32_t> cnt(V.nc), il((size_t)V.nc * 189);
@@ -839,79 +967,97 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                 for (int b = 0; b < l; ++b) v |= (int)((key >> (3 * b + a)) & 1u) << b;
                 return v;
             };
-            std::vector<std::vector<std::pair<int, int>>> byoff(343);
+            std::vector<int> pcls, pgrp;  // per (O, t): class code and symmetry element
+            std::vector<char> used(343, 0);
             for (int O = 0; O < V.nc; ++O)
                 for (int t = 0; t < cnt[O]; ++t) {
-                    int S = il[(size_t)O * 189 + t];
-                    int o = (coord(keys[S], 0) - coord(keys[O], 0) + 3) +
-                            7 * ((coord(keys[S], 1) - coord(keys[O], 1) + 3) + 7 * (coord(keys[S], 2) - coord(keys[O], 2) + 3));
-                    byoff[o].push_back({O, S});
+                    const int S = il[(size_t)O * 189 + t];
+                    int o[3], cc[3];
+                    for (int a = 0; a < 3; ++a) o[a] = coord(keys[S], a) - coord(keys[O], a);
+                    const int g = sym_decompose(o, cc);
+                    const int code = (cc[0] + 3) + 7 * ((cc[1] + 3) + 7 * (cc[2] + 3));
+                    pcls.push_back(code);
+                    pgrp.push_back(g);
+                    used[code] = 1;
                 }
-            std::vector<int32_t> pS, pO;
-            V.ostart.assign(344, 0);
-            for (int o = 0; o < 343; ++o) {
-                V.ostart[o] = (int64_t)pS.size();
-                for (auto &pr : byoff[o]) {
-                    pO.push_back(pr.first);
-                    pS.push_back(pr.second);
+            std::vector<int> cls_of(343, -1);
+            for (int code = 0; code < 343; ++code)
+                if (used[code]) {
+                    cls_of[code] = (int)codes.size();
+                    codes.push_back(code);
+                }
+            V.ncls = (int)codes.size();
+            V.np = (int64_t)pcls.size();
+            V.cbase.assign(V.ncls + 1, 0);
+            for (int code : pcls) V.cbase[cls_of[code] + 1]++;
+            for (int ci = 0; ci < V.ncls; ++ci) V.cbase[ci + 1] += V.cbase[ci];
+            std::vector<int64_t> fill(V.cbase.begin(), V.cbase.end() - 1), ooff(V.nc + 1, 0), oidx(V.np);
+            std::vector<int32_t> hS(V.np);
+            std::vector<uint8_t> hg(V.np), og(V.np);
+            int64_t q = 0;
+            for (int O = 0; O < V.nc; ++O) {
+                ooff[O + 1] = ooff[O] + cnt[O];
+                for (int t = 0; t < cnt[O]; ++t, ++q) {
+                    const int64_t col = fill[cls_of[pcls[q]]]++;
+                    hS[col] = il[(size_t)O * 189 + t];
+                    hg[col] = (uint8_t)pgrp[q];
+                    oidx[q] = col;
+                    og[q] = (uint8_t)pgrp[q];
                 }
             }
-            V.ostart[343] = (int64_t)pS.size();
-            V.np = (int64_t)pS.size();
-            // offsets that occur, by decreasing pair count; the grouping into
-            // batched GEMMs (buckets) is chosen after the operators exist
-            std::vector<int> ord;
-            for (int o = 0; o < 343; ++o)
-                if (V.ostart[o + 1] > V.ostart[o]) ord.push_back(o);
-            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-                return V.ostart[a + 1] - V.ostart[a] > V.ostart[b + 1] - V.ostart[b];
-            });
-            V.ord = ord;
-            V.hpO = pO;
-            V.hpS = pS;
-            m2l_layout(V, 1);  // the widest layout sizes the buffers
-            size_t ncol = (size_t)V.ncol;
             F_TRY(falloc(c, &V.pS, (size_t)V.np));
-            F_TRY(falloc(c, &V.pcol, (size_t)V.np));
+            F_TRY(falloc(c, &V.pg, (size_t)V.np));
             F_TRY(falloc(c, &V.ooff, (size_t)V.nc + 1));
             F_TRY(falloc(c, &V.oidx, (size_t)V.np));
-            if (c->split) {
-                F_TRY(falloc(c, &V.Bbuf32, ncol * P));
-                F_TRY(falloc(c, &V.Cbuf32, ncol * F.nblk * P));
-            } else {
-                F_TRY(falloc(c, &V.Bbuf, ncol * P));
-                F_TRY(falloc(c, &V.Cbuf, ncol * F.nblk * P));
-            }
+            F_TRY(falloc(c, &V.og, (size_t)V.np));
+            F_TRY(cudaMemcpyAsync(V.pS, hS.data(), V.np * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.pg, hg.data(), V.np, cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.oidx, oidx.data(), V.np * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+            F_TRY(cudaMemcpyAsync(V.og, og.data(), V.np, cudaMemcpyHostToDevice, c->s));
             F_TRY(cudaStreamSynchronize(c->s));
         }
-        double Tdt = V.T * c->P.dt;
-        {
-            // operators of the offsets that occur, in bucket order
-            size_t noff = std::max<size_t>(V.ord.size(), 1);
-            size_t nop = noff * F.nblk * P * P;
-            F_TRY(falloc(c, &V.op, nop));
-            int32_t *d_offs = nullptr;
-            F_TRY(falloc(c, &d_offs, noff));
-            if (!V.ord.empty())
-                F_TRY(cudaMemcpyAsync(d_offs, V.ord.data(), V.ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                      c->s));
-            k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, V.s, V.hs, Tdt, c->P.dt, Tdt / 2.0, c->P.c,
-                                                        (int)V.ord.size(), d_offs, V.op);
+        const double Tdt = V.T * c->P.dt;
+        V.Tlen = c->P.c * Tdt;
+        if (V.np > 0) {
+            // canonical operator stacks of the level's classes (FP64)
+            const size_t nop = (size_t)V.ncls * F.R * P;
+            double *op = nullptr;
+            int32_t *d_codes = nullptr;
+            F_TRY(falloc(c, &op, nop));
+            F_TRY(falloc(c, &d_codes, (size_t)V.ncls));
+            F_TRY(cudaMemcpyAsync(d_codes, codes.data(), V.ncls * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
+            k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, V.s, V.hs, V.ho, Tdt, c->P.dt, Tdt / 2.0,
+                                                        c->P.c, V.ncls, d_codes, op);
             F_TRY(cudaGetLastError());
-            if (c->split) {
-                // mixed form: FP32 operators for the emulated-FP32 tensor-core GEMM
-                F_TRY(falloc(c, &V.op32, nop));
-                k_to_float<<<152 * 32, 256, 0, c->s>>>((int64_t)nop, V.op, V.op32);
+            if (!c->split) {
+                V.op = op;
+                F_TRY(falloc(c, &V.Bbuf, (size_t)V.np * P));
+                F_TRY(falloc(c, &V.Cbuf, (size_t)V.np * F.R));
+                V.flops_app = 2.0 * F.R * P * (double)V.np;
+            } else {
+                // BF16 terms of the operators; zero blocks; the FP64 stacks go
+                F_TRY(falloc(c, &V.opt, (size_t)F.nta * V.ncls * F.Rp * F.Kp));
+                k_split_operators<<<152 * 32, 256, 0, c->s>>>(V.ncls, F.R, P, F.Rp, F.Kp, F.nta, op, V.opt);
                 F_TRY(cudaGetLastError());
+                double *d_bm = nullptr;
+                F_TRY(falloc(c, &d_bm, (size_t)V.ncls * F.nblk));
+                k_block_maxabs<<<V.ncls * F.nblk, 256, 0, c->s>>>(P, F.nblk, op, d_bm);
+                F_TRY(cudaGetLastError());
+                std::vector<double> bm((size_t)V.ncls * F.nblk);
+                F_TRY(cudaMemcpyAsync(bm.data(), d_bm, bm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
                 F_TRY(cudaStreamSynchronize(c->s));
-                auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)V.op);
-                if (it != c->allocs.end()) c->allocs.erase(it);
-                cudaFree(V.op);
-                V.op = nullptr;
+                for (void *p : {(void *)op, (void *)d_bm}) {
+                    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+                    if (it != c->allocs.end()) c->allocs.erase(it);
+                    cudaFree(p);
+                }
+                F_TRY(falloc(c, &V.Bt, (size_t)F.ntb * V.np * F.Kp));
+                F_TRY(falloc(c, &V.C32, (size_t)V.np * F.R));
+                F_TRY(tc_make_map(&V.mapA, V.opt, (int64_t)F.nta * V.ncls * F.Rp, F.Kp, kTcBM));
+                F_TRY(m2l_tune(c, V, bm));
             }
         }
-        V.Tlen = c->P.c * Tdt;
-        if (V.np > 0) F_TRY(m2l_tune_and_finalize(c, V));
     }
     return cudaStreamSynchronize(c->s);
 }
@@ -936,34 +1082,30 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
         int kl = (k + 1) / span - 1;
         FmmLevel &V = F.lev[l];
         const TreeLevel &T = c->tree.levels[l];
-        // M2L for source interval kl of this level: gather, one GEMM per
-        // offset, per-cell reduction into the locals (near future) and G
+        // M2L for source interval kl of this level: gather (permuted by each
+        // column's symmetry), one GEMM per symmetry class, per-cell
+        // reduction into the locals (near future) and G
         if (V.np > 0) {
-            const int R = F.nblk * P;
             cudaEvent_t ev;
             phase_begin(c, &ev);
-            cublasStatus_t st;
-            if (c->split) {
-                // FP32 operands, FP32-accurate products on the BF16 tensor
-                // cores (three BF16 terms per operand), FP64 locals
-                k_m2l_gather<float><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf32);
-                st = m2l_gemms(c, V);
-                k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf32,
-                                                         V.ring, V.G);
-            } else {
-                k_m2l_gather<double><<<152 * 8, 256, 0, s>>>(V.np, P, V.pS, V.pcol, V.M, V.Bbuf);
-                st = m2l_gemms(c, V);
-                k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.Cbuf,
-                                                          V.ring, V.G);
-            }
-            if (st != CUBLAS_STATUS_SUCCESS) {
-                c->err = "cuBLAS status " + std::to_string((int)st) + " in the M2L GEMM";
-                return cudaErrorUnknown;
-            }
+            const int64_t n = V.np * P;
+            const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+            if (c->split)
+                k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt);
+            else
+                k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf);
+            F_TRY(cudaGetLastError());
+            F_TRY(m2l_products(c, V));
+            if (c->split)
+                k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.og,
+                                                         F.iperm, V.C32, V.ring, V.G);
+            else
+                k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx,
+                                                          V.og, F.iperm, V.Cbuf, V.ring, V.G);
+            F_TRY(cudaGetLastError());
             phase_end(c, PH_M2L, ev);
             c->launches[PH_M2L] += 1;
-            c->m2l_flops += 2.0 * (double)R * P * (double)V.np;  // algorithmic (unpadded) flops
-            F_TRY(cudaGetLastError());
+            c->m2l_flops += V.flops_app;
         } else {
             F_TRY(cudaMemsetAsync(V.G, 0, (size_t)d * V.nc * P * sizeof(double), s));
         }
@@ -991,7 +1133,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
         FmmLevel &Pv = F.lev[l], &Cv = F.lev[l + 1];
         k_l2l<<<Cv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, c->tree.levels[l].ckey, Cv.nc, c->tree.levels[l + 1].ckey,
                                       Pv.ring + (size_t)(kp % F.nslot) * Pv.nc * P,
-                                      Cv.ring + (size_t)(kc % F.nslot) * Cv.nc * P, Cv.Sm, F.Tm, kc & 1);
+                                      Cv.ring + (size_t)(kc % F.nslot) * Cv.nc * P, Cv.So, F.Tm, kc & 1);
         F_TRY(cudaGetLastError());
     }
     // L2P for observation interval k + 1

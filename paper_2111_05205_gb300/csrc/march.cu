@@ -17,10 +17,20 @@ __device__ __forceinline__ double incident_term(const Incident &in, const double
 {
     double kx = in.k[0] * xc[0] + in.k[1] * xc[1] + in.k[2] * xc[2];
     double s = alpha * in.dt - in.t0 - kx / in.c;
-    double a = s / in.width;
-    double f = exp(-a * a);
+    double f, df;
+    if (in.shape == 0) {
+        double a = s / in.width;
+        f = exp(-a * a);
+        df = -2.0 * a / in.width * f;
+    } else {
+        // raised cosine 0.5 (1 - cos(2 pi c s / width)) for 0 <= c s <= width
+        // (Eq. uin with ct - x_1 = c s), zero elsewhere
+        const double w = 2.0 * 3.14159265358979323846 * in.c / in.width, cs = in.c * s;
+        const bool on = cs >= 0.0 && cs <= in.width;
+        f = on ? 0.5 * (1.0 - cos(w * s)) : 0.0;
+        df = on ? 0.5 * w * sin(w * s) : 0.0;
+    }
     if (!in.bie) return f;
-    double df = -2.0 * a / in.width * f;
     double kn = in.k[0] * n[0] + in.k[1] * n[1] + in.k[2] * n[2];
     // d/dn_x f(t - k.x/c) = -(k.n/c) f';  c^-1 d/dt f = f'/c
     return -(1.0 + kn) / in.c * df;

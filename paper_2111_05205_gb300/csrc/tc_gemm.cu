@@ -21,7 +21,7 @@
 //     and K step of a stage, then tcgen05.commit frees the stage;
 //   warps 2-5: epilogue; each reads its 32 TMEM lanes (tcgen05.ld 32x32b)
 //     and stores the FP32 results, one coalesced 128-byte row per column.
-// Every mbarrier wait gives up after kWaitNs of global time, sets bit 1 of
+// Every mbarrier wait gives up after kWaitNs of global time, sets bit 3 of
 // *err and lets the CTA finish: TMA copies in flight are waited for (with
 // the same bound) and the TMEM columns are freed before the CTA exits.
 #include <cuda.h>
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int kc = 0; kc < K; ++kc) {
                 const int s = kc % nstage;
                 if (kc >= nstage && !mbar_wait(empty0 + 8 * s, ((kc / nstage) - 1) & 1)) {
-                    atomicOr(g.err, 2);
+                    atomicOr(g.err, 8);
                     break;
                 }
                 const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             // every copy issued has landed before the CTA may exit
             for (int kc = (issued > nstage ? issued - nstage : 0); kc < issued; ++kc)
-                if (!mbar_wait(full0 + 8 * (kc % nstage), (kc / nstage) & 1)) atomicOr(g.err, 2);
+                if (!mbar_wait(full0 + 8 * (kc % nstage), (kc / nstage) & 1)) atomicOr(g.err, 8);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int kc = 0; kc < K; ++kc) {
                 const int s = kc % nstage;
                 if (!mbar_wait(full0 + 8 * s, (kc / nstage) & 1)) {
-                    atomicOr(g.err, 2);
+                    atomicOr(g.err, 8);
                     break;
                 }
                 tc_fence_after();
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(192, 1)
         const bool ok = mbar_wait(accf, 0);
         tc_fence_after();
         if (!ok) {
-            if (lane == 0) atomicOr(g.err, 2);
+            if (lane == 0) atomicOr(g.err, 8);
         } else {
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {

@@ -25,6 +25,7 @@ enum { KIND_CU = 0, KIND_CW = 1, KIND_UB = 2, KIND_WB = 3 };
 struct Incident {
     int on;
     int bie;
+    int shape;  // 0: Gaussian exp(-(s/width)^2); 1: raised cosine of length width (Section 5.1.1)
     double k[3];
     double t0, width, c, dt;
 };
@@ -47,62 +48,6 @@ struct Tree {
     int32_t *perm = nullptr;      // [ns] element at each sorted position
     int32_t *e2c = nullptr;       // [ns] leaf cell of each element (element numbering)
     std::vector<TreeLevel> levels;
-};
-
-// A group of cell offsets whose M2L GEMMs run as one batched call.
-struct FmmBucket {
-    int first = 0, count = 0;    // range in the level's offset order
-    int64_t n = 0;               // columns per offset (the group's largest pair count)
-};
-
-// One level of the space-time FMM (device arrays; levels 2..L).
-struct FmmLevel {
-    int nc = 0;
-    double s = 0, hs = 0;        // cell side, interpolation half-width
-    int T = 0;                   // steps per interval
-    double Tlen = 0;             // c x interval length (T of Formula 1)
-    double *M = nullptr;         // [nc][P] moment of the current source interval
-    double *ring = nullptr;      // [mu+2][nc][P] locals L_k .. L_{k+mu+1}
-    double *D = nullptr;         // [d][nc][P] derivative locals L^(p)
-    double *A = nullptr;         // [n_d][nc][P] auxiliary locals L^(p,m)
-    double *G = nullptr;         // [d][nc][P] contributions L^(p)_{k+mu+1,k}
-    double *op = nullptr;        // [offsets in bucket order][mu+1+d][P][P] M2L operators
-    double *Sm = nullptr;        // [2][ps][ps] transfer to the parent level
-    // interaction pairs grouped by offset for the GEMM form of the M2L
-    int64_t np = 0;              // pairs
-    std::vector<int64_t> ostart; // [344] first pair of each offset
-    int32_t *pS = nullptr;       // [np] source cell of each pair
-    int64_t ncol = 0;            // columns of the gathered-moment buffer
-    std::vector<int> ord;        // offsets with pairs, by decreasing pair count
-    std::vector<int64_t> colbase;  // [343] first column of each offset's slab
-    std::vector<FmmBucket> buckets;
-    int nbk = 1;                 // buckets chosen by the autotuner
-    std::vector<std::pair<int, float>> tune;  // (buckets, ms) measured at setup
-    std::vector<int32_t> hpO, hpS;            // host copies of the pairs until the layout is final
-    int64_t *pcol = nullptr;     // [np] padded column of each pair
-    int64_t *ooff = nullptr;     // [nc+1] pairs of each observation cell (CSR)
-    int64_t *oidx = nullptr;     // [np] their padded columns
-    double *Bbuf = nullptr;      // [np][P] gathered moments
-    double *Cbuf = nullptr;      // [np][(mu+1+d) P] operator stack x moment
-    float *op32 = nullptr;       // mixed form: FP32 operators, operands and products
-    float *Bbuf32 = nullptr;
-    float *Cbuf32 = nullptr;
-    int64_t flops_per_interval = 0;  // 2 (mu+1+d) P^2 x pairs
-};
-
-struct Fmm {
-    bool on = false;
-    struct cublasContext *blas = nullptr;  // cuBLAS handle
-    int L = 0, ps = 0, pt = 0, P3 = 0, P = 0, mu = 0, Lt = 0, nblk = 0, nd = 0, nslot = 0;
-    double rho = 0;
-    std::vector<FmmLevel> lev;
-    double *At = nullptr, *As = nullptr, *Dv = nullptr, *Dn = nullptr;  // [ns][P3]
-    double *tl = nullptr, *dtl = nullptr;  // [Lt][8] time basis at the interval's positions
-    double *wk = nullptr;                   // [d+2] w^{kappa,d}
-    double *Tm = nullptr;                   // [2][pt][pt] time transfer
-    double *cmp = nullptr;                  // c_m^p(k) of the current call
-    double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
-    int far_k = -1;                         // leaf interval the far field belongs to
 };
 
 // Split-precision tensor-core GEMM (tc_gemm.cu): one output tile of at most
@@ -130,7 +75,7 @@ struct TcGemmArgs {
     int64_t ldc;
     float *C;
     const TcTile *tiles;
-    int *err;                         // bit 1: a wait gave up
+    int *err;                         // bit 3 (value 8) is set when a pipeline wait gave up
 };
 
 cudaError_t tc_make_map(CUtensorMap *map, const void *base, int64_t rows, int kp, int box_rows);
@@ -138,6 +83,72 @@ int tc_stages(int nta, int ntb, int bn);
 size_t tc_smem_bytes(int nta, int ntb, int bn, int nstage);
 cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const TcGemmArgs &a, int ntiles, int bn,
                            cudaStream_t s);
+
+// One level of the space-time FMM (device arrays; levels 2..L).
+//
+// M2L layout: the cell offsets o = S - O of the level's interaction pairs
+// fall into classes of the cube's symmetry group (axis permutations and
+// reflections); every offset is g(c) for the class's canonical offset c
+// (|c_0| >= |c_1| >= |c_2| >= 0) and one fixed element g.  Because g maps
+// the interpolation nodes onto themselves, the operator of o is the
+// canonical one with its node indices permuted, so one operator per class
+// serves all its offsets: a pair's moment enters the GEMM permuted by g and
+// its product leaves it permuted back (see fmm.cu).
+struct FmmLevel {
+    int nc = 0;
+    double s = 0, hs = 0, ho = 0;  // cell side, source / observation interpolation half-widths
+    int T = 0;                   // steps per interval
+    double Tlen = 0;             // c x interval length (T of Formula 1)
+    double *M = nullptr;         // [nc][P] moment of the current source interval
+    double *ring = nullptr;      // [mu+2][nc][P] locals L_k .. L_{k+mu+1}
+    double *D = nullptr;         // [d][nc][P] derivative locals L^(p)
+    double *A = nullptr;         // [n_d][nc][P] auxiliary locals L^(p,m)
+    double *G = nullptr;         // [d][nc][P] contributions L^(p)_{k+mu+1,k}
+    double *Sm = nullptr;        // [2][ps][ps] source-box transfer to the parent level (M2M)
+    double *So = nullptr;        // [2][ps][ps] observation-box transfer from the parent level (L2L)
+    // interaction pairs in GEMM column order: grouped by symmetry class
+    int64_t np = 0;              // pairs (= GEMM columns)
+    int ncls = 0;                // classes with pairs
+    std::vector<int64_t> cbase;  // [ncls+1] first column of each class
+    int32_t *pS = nullptr;       // [np] source cell of each column
+    uint8_t *pg = nullptr;       // [np] symmetry element of each column
+    int64_t *ooff = nullptr;     // [nc+1] columns of each observation cell (CSR)
+    int64_t *oidx = nullptr;     // [np] their columns, in interaction-list order
+    uint8_t *og = nullptr;       // [np] their symmetry elements
+    double *op = nullptr;        // FP64 form: [ncls][(mu+1+d) P][P] canonical operator stacks
+    double *Bbuf = nullptr;      // FP64 form: [np][P] gathered (permuted) moments
+    double *Cbuf = nullptr;      // FP64 form: [np][(mu+1+d) P] products
+    // tensor-core forms: split terms of operators and moments, FP32 products
+    uint16_t *opt = nullptr;     // [nta][ncls][Rp][Kp] BF16 operator terms
+    uint16_t *Bt = nullptr;      // [ntb][np][Kp] BF16 moment terms
+    float *C32 = nullptr;        // [np][(mu+1+d) P] products
+    TcTile *tiles = nullptr;     // [ntiles] GEMM tiles (zero operator blocks skipped)
+    int ntiles = 0;
+    int tile_n = 128;            // tile width chosen by the setup-time tuner
+    std::vector<std::pair<int, float>> tune;  // (tile width, ms) measured at setup
+    CUtensorMap mapA{}, mapB{};
+    double flops_app = 0;        // algorithmic flops of one M2L application, 2 (mu+1+d) P^2 np
+};
+
+struct Fmm {
+    bool on = false;
+    struct cublasContext *blas = nullptr;  // cuBLAS handle (FP64 form)
+    int L = 0, ps = 0, pt = 0, P3 = 0, P = 0, mu = 0, Lt = 0, nblk = 0, nd = 0, nslot = 0;
+    int R = 0, Rp = 0, Kp = 0;              // operator rows, rows padded to 128, K padded to 64
+    int nta = 0, ntb = 0, nprod = 0;        // tensor-core forms: split terms and products
+    int prod[kTcMaxProd] = {0};
+    int16_t *perm = nullptr;                // [48][P3] node permutation of each symmetry element
+    int16_t *iperm = nullptr;               // [48][P3] its inverse
+    double rho = 0;
+    std::vector<FmmLevel> lev;
+    double *At = nullptr, *As = nullptr, *Dv = nullptr, *Dn = nullptr;  // [ns][P3]
+    double *tl = nullptr, *dtl = nullptr;  // [Lt][8] time basis at the interval's positions
+    double *wk = nullptr;                   // [d+2] w^{kappa,d}
+    double *Tm = nullptr;                   // [2][pt][pt] time transfer
+    double *cmp = nullptr;                  // c_m^p(k) of the current call
+    double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
+    int far_k = -1;                         // leaf interval the far field belongs to
+};
 
 struct Pending {
     int phase;

@@ -16,7 +16,8 @@ class Solver:
     "bmbie"), ``phi`` per-element boundary condition (1 Neumann, 0
     Dirichlet), ``known`` samples of the known data at t_1..t_{nt-1}
     [(nt-1), ns] or None,
-    ``incident`` (direction, t0, width) of a Gaussian plane pulse or None.
+    ``incident`` (direction, t0, width[, shape]) of a plane pulse (shape 0
+    Gaussian of that width, 1 raised cosine of that length) or None.
     ``fmm``: (ps, pt, mu) to evaluate the far part with the space-time FMM
     (needs ``depth`` >= 2; mu = 0 picks the smallest valid value).
     ``stream``: a cudaStream_t handle (int) or None.  ``precision``: 0 /
@@ -46,8 +47,9 @@ class Solver:
             if known is not None:
                 abi.tdbem_set_known(self.ctx, known)
             if incident is not None:
-                direction, t0, width = incident
-                abi.tdbem_set_incident_plane(self.ctx, direction, t0, width, 0)
+                direction, t0, width = incident[:3]
+                shape = incident[3] if len(incident) > 3 else 0
+                abi.tdbem_set_incident_plane(self.ctx, direction, t0, width, shape)
             abi.tdbem_prepare(self.ctx)
         except Exception:
             abi.tdbem_destroy(self.ctx)

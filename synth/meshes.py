@@ -1,4 +1,4 @@
-"""Seeded triangle meshes: icospheres and ellipsoids.
+"""Seeded triangle meshes: icospheres, geodesic spheres and ellipsoids.
 
 Every mesh is returned as ``(xyz, tri)`` with ``xyz`` a float64 array
 ``[nv, 3]`` and ``tri`` an int32 array ``[ns, 3]``.  Triangles are ordered
@@ -62,6 +62,38 @@ def icosphere(subdiv, radius=1.0, center=(0.0, 0.0, 0.0)):
         f = np.array(nf, dtype=np.int64)
     xyz = np.asarray(verts, dtype=np.float64) * float(radius) + np.asarray(center, dtype=np.float64)
     return xyz, f.astype(np.int32)
+
+
+def geodesic(n, radius=1.0, center=(0.0, 0.0, 0.0)):
+    """Geodesic sphere with 20 n^2 flat triangles: every face of the
+    icosahedron cut into n^2 triangles by its n-fold edge subdivision, the
+    vertices pushed out to the sphere (n = 12, 16, 24 give the element
+    counts 2880, 5120 and 11520 of the paper's sphere, Section 5.1.1)."""
+    v, f = _icosahedron()
+    verts, index = [], {}
+
+    def vert(a, b, c, i, j):
+        # point i/n along a->b and j/n along a->c of face (a, b, c), keyed
+        # by its barycentric weights on the global vertices (shared edges)
+        wts = {a: n - i - j, b: i, c: j}
+        key = tuple(sorted((g, w) for g, w in wts.items() if w))
+        if key not in index:
+            p = sum(v[g] * w for g, w in wts.items()) / n
+            index[key] = len(verts)
+            verts.append(p / np.linalg.norm(p))
+        return index[key]
+
+    tris = []
+    for a, b, c in f:
+        for i in range(n):
+            for j in range(n - i):
+                p0, p1, p2 = vert(a, b, c, i, j), vert(a, b, c, i + 1, j), vert(a, b, c, i, j + 1)
+                tris.append([p0, p1, p2])
+                if i + j + 1 < n:
+                    p3 = vert(a, b, c, i + 1, j + 1)
+                    tris.append([p1, p3, p2])
+    xyz = np.asarray(verts) * float(radius) + np.asarray(center, dtype=np.float64)
+    return xyz, np.asarray(tris, dtype=np.int32)
 
 
 def ellipsoid(subdiv, seed, lo=0.5, hi=1.5):

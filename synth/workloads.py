@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .meshes import ellipsoid, icosphere, mean_edge
+from .meshes import ellipsoid, geodesic, icosphere, mean_edge
 
 
 @dataclass
@@ -35,7 +35,7 @@ class Workload:
     bie: str  # "obie" | "bmbie"
     bc: str  # "dirichlet" | "neumann"
     excitation: str  # "uniform" | "plane"
-    sigma: float
+    sigma: float  # Gaussian width, or the raised cosine's pulse length (shape 1)
     t0: float = 0.0
     direction: np.ndarray = field(default_factory=lambda: np.array([1.0, 0.0, 0.0]))
     # space-time FMM parameters (leaf level, nodes per dimension, mu)
@@ -43,6 +43,8 @@ class Workload:
     ps: int = 0
     pt: int = 0
     mu: int = 8
+    # incident pulse profile: 0 Gaussian, 1 raised cosine (Section 5.1.1)
+    shape: int = 0
 
     @property
     def ns(self):
@@ -87,6 +89,20 @@ def workload(name, nt=None):
                      "bmbie", "neumann", "plane", sigma=sig,
                      t0=4 * sig + float(np.linalg.norm(xyz, axis=1).max()) / c,
                      direction=_unit(rng), depth=5, ps=5, pt=5)
+    elif name.startswith("paper_sphere"):
+        # the sphere example of Section 5.1.1: radius 0.5, centre (0.5, 0, 0),
+        # geodesic mesh of 2880 / 5120 / 11520 elements, dt = 0.04 / 0.03 /
+        # 0.02 and Nt = 240 / 320 / 480 (analysis time 9.6), raised-cosine
+        # plane pulse along +x_1 of length 0.5 with t0 = 0 (Eq. uin);
+        # e.g. paper_sphere2880_bmbie_d2_hard
+        parts = name.split("_")
+        ns = int(parts[1][len("sphere"):])
+        n, dt, nt = {2880: (12, 0.04, 240), 5120: (16, 0.03, 320), 11520: (24, 0.02, 480),
+                     80: (2, 0.25, 40), 320: (4, 0.12, 80)}[ns]
+        xyz, tri = geodesic(n, radius=0.5, center=(0.5, 0.0, 0.0))
+        bc = {"hard": "neumann", "soft": "dirichlet"}[parts[4]]
+        w = Workload(name, xyz, tri, c, dt, nt, int(parts[3][1:]), parts[2], bc, "plane", sigma=0.5, t0=0.0,
+                     direction=np.array([1.0, 0.0, 0.0]), shape=1)
     elif name.startswith("ellipsoid") and "_plane" in name:
         # small seeded ellipsoids for tests, e.g. ellipsoid320_bmbie_d2_hard_plane_s7
         parts = name.split("_")

@@ -23,7 +23,7 @@ def phi_of(w):
 
 def gpu_solver(w, stream=None, precision=0, depth=0, fmm=None):
     from paper_2111_05205_gb300 import Solver
-    inc = (w.direction, w.t0, w.sigma) if w.excitation == "plane" else None
+    inc = (w.direction, w.t0, w.sigma, w.shape) if w.excitation == "plane" else None
     known = known_samples(w) if w.excitation == "uniform" else None
     return Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi_of(w), known=known, incident=inc,
                   stream=stream, precision=precision, depth=depth, fmm=fmm)

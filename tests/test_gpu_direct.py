@@ -46,6 +46,9 @@ MOT_CASES = [
     "ellipsoid80_bmbie_d2_hard_plane_s7",
     "ellipsoid80_bmbie_d1_soft_plane_s5",
     "ellipsoid320_bmbie_d2_hard_plane_s11",
+    # the paper's sphere (Section 5.1.1) with its raised-cosine pulse
+    "paper_sphere80_bmbie_d2_hard",
+    "paper_sphere80_bmbie_d1_soft",
 ]
 
 

@@ -60,23 +60,24 @@ def test_tc_gemm_matches_numpy(m, n, k, nta, ntb, prod, fmt, bn):
 
 def test_tc_gemm_split_reaches_fp32_accuracy():
     """Three BF16 terms per operand with the six leading products give a
-    product of the FP64 operands to about FP32 accuracy (FP32 accumulation
-    over K = 512), several times better than two terms with three products."""
+    product of the FP64 operands to about FP32 accuracy, far better than two
+    terms with three products (~2^-17).  Positive operands and a short K, so
+    that the FP32 accumulation (~2^-24 per add) does not hide the products'
+    own error."""
     from paper_2111_05205_gb300 import abi, build
     build.build()
     rng = np.random.default_rng(5)
-    m, n, k = 256, 128, 512
-    A = rng.standard_normal((m, k))
-    B = rng.standard_normal((n, k))
+    m, n, k = 256, 128, 64
+    A = rng.uniform(0.5, 1.0, (m, k))
+    B = rng.uniform(0.5, 1.0, (n, k))
     ref = B @ A.T
-    bound = np.abs(B) @ np.abs(A).T
     ab3, _ = _split(A, 3, 1)
     bb3, _ = _split(B, 3, 1)
     c3 = abi.tdbem_tc_gemm_check(ab3, bb3, [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)])
     ab2, _ = _split(A, 2, 1)
     bb2, _ = _split(B, 2, 1)
     c2 = abi.tdbem_tc_gemm_check(ab2, bb2, [(0, 0), (0, 1), (1, 0)])
-    e3 = np.max(np.abs(c3 - ref) / bound)
-    e2 = np.max(np.abs(c2 - ref) / bound)
-    assert e3 < 4e-6, e3
-    assert e3 < 0.25 * e2, (e3, e2)
+    e3 = np.max(np.abs(c3 - ref) / ref)
+    e2 = np.max(np.abs(c2 - ref) / ref)
+    assert e3 < 1e-6, e3
+    assert e3 < 0.1 * e2, (e3, e2)

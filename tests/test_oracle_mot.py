@@ -87,3 +87,36 @@ def test_bm_incident_operator():
 
     fd = (uin(xc + h * n, t) - uin(xc - h * n, t)) / (2 * h) - (uin(xc, t + h) - uin(xc, t - h)) / (2 * h) / w.c
     assert np.allclose(e, fd, atol=1e-8)
+
+
+def test_raised_cosine_pulse():
+    """The pulse of Section 5.1.1: zero outside 0 <= c t - x_1 <= Lambda,
+    peak 1 at the middle, area Lambda / (2c) in time, C^1 at both ends, and
+    the Burton-Miller right-hand side (d/dn - c^-1 d/dt) u_in by finite
+    differences on the paper-shaped sphere."""
+    L, c = 0.5, 1.0
+    t = np.linspace(-1.0, 2.0, 300001)
+    f = mot.raised_cosine(t, L, c, 0.0)
+    assert np.all(f[(t < 0) | (t > L / c)] == 0.0)
+    assert abs(mot.raised_cosine(np.array([L / (2 * c)]), L, c, 0.0)[0] - 1.0) < 1e-15
+    assert abs(np.trapezoid(f, t) - L / (2 * c)) < 1e-9
+    h = 1e-7
+    for edge in (0.0, L / c):
+        assert abs(mot.draised_cosine(np.array([edge]), L, c, 0.0)[0]) < 1e-12
+        fd = (mot.raised_cosine(np.array([edge + h]), L, c, 0.0) - mot.raised_cosine(np.array([edge - h]), L, c, 0.0)) / (2 * h)
+        assert abs(fd[0]) < 1e-5
+    w = workload("paper_sphere80_bmbie_d2_hard")
+    v, xc, n, _ = oc.geometry(w.xyz, w.tri)
+    for a in (1, 2, 3):
+        e = mot.incident_rhs(w, xc, n, a)
+        tt = a * w.dt
+
+        def uin(x, t):
+            return mot.raised_cosine(t - (x @ w.direction) / w.c, w.sigma, w.c, w.t0)
+
+        hh = 1e-6
+        fd = (uin(xc + hh * n, tt) - uin(xc - hh * n, tt)) / (2 * hh) - (uin(xc, tt + hh) - uin(xc, tt - hh)) / (2 * hh) / w.c
+        # atol: central differences across the support's ends, where the
+        # pulse's second derivative jumps (O(h f''))
+        assert np.allclose(e, fd, atol=1e-4)
+        assert np.abs(e).max() > 0.1
