@@ -83,7 +83,9 @@ typedef struct {
     int32_t depth;        /* leaf level L of the spatial hierarchy (root = 0); 0 = none */
     double solver_tol;    /* bound on the zero-lag solve's relative error (0: 1e-16) */
     int32_t solver_maxit; /* cap on zero-lag iterations (0: 200) */
-    int32_t reserved;
+    int32_t precond;      /* zero-lag solver: 0 = Jacobi sweeps; 1 = the learned sparse
+                             approximate inverse that tdbem_set_precond installs where it
+                             needs fewer sweeps than Jacobi (Jacobi stays its fallback) */
 } tdbem_params;
 
 /* Per-phase device time (ms) and launch counts accumulated since the last
@@ -113,6 +115,15 @@ typedef struct {
     int32_t m2l_tile_n[11];        /* FMM, tensor-core forms: GEMM tile width (columns) per level
                                       chosen by the setup-time tuner (0 for levels without
                                       interaction pairs or in the FP64 form) */
+    double ms_gemm;                /* FMM: the M2L GEMM launches alone (tensor-core kernel, or the
+                                      FP64 form's DGEMMs) */
+    int64_t launches_gemm;         /* FMM: GEMM launches */
+    double gemm_tc_flops;          /* FMM: tensor-pipe flops the split requires, m2l_flops x
+                                      m2l_products (K and tile padding not counted) */
+    int32_t m2l_products;          /* FMM: BF16 products per FP64 product (6, 3, 1; 1 = FP64 form) */
+    int32_t reserved2;
+    int64_t launches_far_kernels;  /* FMM: kernel launches of the far-field passes (P2M, M2L gather,
+                                      GEMM, reduction, recurrence, M2M, L2L, L2P) */
 } tdbem_stats;
 
 /* Creates a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -255,7 +266,8 @@ int tdbem_sai_weights(tdbem_sai *sai, float *inout, int64_t *count, int32_t set)
 /* Installs the network's M as the context's zero-lag solver (sweeps
  * x <- x + M (b - A x), one launch each, count from ||I - M A||_inf so that
  * the error stays below solver_tol) when that takes fewer sweeps than
- * Jacobi; otherwise Jacobi stays.  *use_sai, *sweeps, *contraction report the choice. */
+ * Jacobi; otherwise Jacobi stays.  *use_sai, *sweeps, *contraction report the choice.
+ * ERR_STATE for a context created with precond = 0 (Jacobi only) or not prepared. */
 int tdbem_set_precond(tdbem_ctx *ctx, const tdbem_sai *sai, int32_t *use_sai, int32_t *sweeps, double *contraction);
 
 /* Checkpoint and resume at any step boundary (an addition of the library).
@@ -296,6 +308,20 @@ int tdbem_get_coefficients(const tdbem_ctx *ctx, int32_t kind, const int32_t *ro
  * Eq. target_m2l; with the Burton-Miller operator for BMBIE).  out may be NULL
  * to query first_step and nsteps (= Lt).  ERR_STATE without algo 1. */
 int tdbem_get_far(const tdbem_ctx *ctx, double *out, int32_t *first_step, int32_t *nsteps);
+
+/* Field off the boundary (Section 2.1: the representation formula of the
+ * exterior problem, of which Eq. bie is the limit on S), discretised like the
+ * boundary equation:
+ *   u(x_p, t_a) = u_in(x_p, t_a) + sum_j sum_{g=1}^{a} (C_U^(g)(x_p, E_j) q_j^{a-g}
+ *                                                     - C_W^(g)(x_p, E_j) u_j^{a-g})
+ * with the compact coefficients of the marching evaluated at x_p and the
+ * solution histories of the steps taken; u_in is the incident pulse, if any.
+ * points[npts*3] host (copied), points of the exterior domain off S;
+ * out[na*npts] host, out[(a - a0)*npts + p] for steps a = a0 .. a0+na-1,
+ * 1 <= a0, a0+na-1 <= steps taken.  Whatever the BIE used to solve, the field
+ * is the single- and double-layer representation.  ERR_ARG for an empty set,
+ * steps outside that range or a point on S; synchronous. */
+int tdbem_eval_field(const tdbem_ctx *ctx, const double *points, int32_t npts, int32_t a0, int32_t na, double *out);
 
 /* Zero-lag matrix A of Eq. linear as dense host rows out[ns*ns] (small ns only). */
 int tdbem_get_zero_lag(const tdbem_ctx *ctx, double *out);

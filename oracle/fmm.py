@@ -151,23 +151,50 @@ def tri_rule(n):
     return np.array(pts), np.array(wts)
 
 
+def _lagrange_many(nodes, xi):
+    """Lagrange basis values and derivatives at the points xi [nq] -> [nq, p]
+    (the same recurrence as ``lagrange``, over all points at once)."""
+    p = len(nodes)
+    val = np.ones((len(xi), p))
+    der = np.zeros((len(xi), p))
+    for a in range(p):
+        for b in range(p):
+            if b == a:
+                continue
+            f = (xi - nodes[b]) / (nodes[a] - nodes[b])
+            der[:, a] = der[:, a] * f + val[:, a] / (nodes[a] - nodes[b])
+            val[:, a] *= f
+    return val, der
+
+
 def p2m_weights(H, l):
     """A^tau_{jb} = int_{E_j} ell_b dS and A^sigma_{jb} = int_{E_j} n_y.grad ell_b dS
-    for the level-l box of each element's cell (moment of Section 3)."""
+    for the level-l source box of each element's cell (moment of Section 3),
+    by the collapsed Gauss rule on each triangle (all quadrature points of an
+    element at once)."""
     pts, wts = tri_rule(2 * H.ps + 2)
     ns = H.xc.shape[0]
-    P = H.ps ** 3
+    p = H.ps
+    P = p ** 3
     At = np.zeros((ns, P))
     As = np.zeros((ns, P))
     V = H.v.reshape(-1, 3, 3)
     for j in range(ns):
         a, b, c = V[j]
         area2 = np.linalg.norm(np.cross(b - a, c - a))
-        for (s, t), wq in zip(pts, wts):
-            y = a + s * (b - a) + t * (c - a)
-            val, grad = H.space_basis(l, H.cell[l][j], y)
-            At[j] += wq * area2 * val
-            As[j] += wq * area2 * (grad @ H.n[j])
+        Y = a[None, :] + pts[:, :1] * (b - a)[None, :] + pts[:, 1:2] * (c - a)[None, :]  # [nq, 3]
+        xi = (Y - H.centre(l, H.cell[l][j])[None, :]) / H.hs[l]
+        L = [_lagrange_many(H.ws, xi[:, k]) for k in range(3)]  # per axis ([nq, p], [nq, p])
+        # ell_b = ell_{b1}(x) ell_{b2}(y) ell_{b3}(z), b = b1 + p (b2 + p b3)
+        v0, v1, v2 = L[0][0], L[1][0], L[2][0]
+        d0, d1, d2 = L[0][1], L[1][1], L[2][1]
+        val = np.einsum("qi,qj,qk->qkji", v0, v1, v2).reshape(-1, P)
+        g0 = np.einsum("qi,qj,qk->qkji", d0, v1, v2).reshape(-1, P) / H.hs[l]
+        g1 = np.einsum("qi,qj,qk->qkji", v0, d1, v2).reshape(-1, P) / H.hs[l]
+        g2 = np.einsum("qi,qj,qk->qkji", v0, v1, d2).reshape(-1, P) / H.hs[l]
+        n = H.n[j]
+        At[j] = area2 * (wts @ val)
+        As[j] = area2 * (wts @ (g0 * n[0] + g1 * n[1] + g2 * n[2]))
     return At, As
 
 

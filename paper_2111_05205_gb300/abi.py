@@ -29,7 +29,7 @@ class tdbem_params(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("nt", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("bie", ctypes.c_int32), ("algo", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("ps", ctypes.c_int32), ("pt", ctypes.c_int32), ("mu", ctypes.c_int32), ("depth", ctypes.c_int32),
-                ("solver_tol", ctypes.c_double), ("solver_maxit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("solver_tol", ctypes.c_double), ("solver_maxit", ctypes.c_int32), ("precond", ctypes.c_int32)]
 
 
 class tdbem_stats(ctypes.Structure):
@@ -41,7 +41,10 @@ class tdbem_stats(ctypes.Structure):
                 ("solve_contraction", ctypes.c_double), ("ms_prepare", ctypes.c_double),
                 ("ms_far", ctypes.c_double), ("launches_far", ctypes.c_int64), ("fmm_lt", ctypes.c_int32),
                 ("fmm_mu", ctypes.c_int32), ("ms_m2l", ctypes.c_double), ("launches_m2l", ctypes.c_int64),
-                ("m2l_flops", ctypes.c_double), ("m2l_tile_n", ctypes.c_int32 * 11)]
+                ("m2l_flops", ctypes.c_double), ("m2l_tile_n", ctypes.c_int32 * 11),
+                ("ms_gemm", ctypes.c_double), ("launches_gemm", ctypes.c_int64), ("gemm_tc_flops", ctypes.c_double),
+                ("m2l_products", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("launches_far_kernels", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +94,7 @@ SIGNATURES = {
     "tdbem_sync": (ctypes.c_int, [_P]),
     "tdbem_zero_lag_solve_static": (ctypes.c_int, [_P, _P, _P, _I]),
     "tdbem_grid_barrier_probe": (ctypes.c_int, [_I, _I, ctypes.POINTER(_I)]),
+    "tdbem_eval_field": (ctypes.c_int, [_P, _P, _I, _I, _I, _P]),
     "tdbem_tc_gemm_check": (ctypes.c_int, [_I, _I, _I, _I, _I, _P, _I, _I, _I, _P, _P, _P]),
 }
 
@@ -392,3 +396,12 @@ def tdbem_tc_gemm_check(a, b, prod, fmt=1, bn=128):
     if code != TDBEM_OK:
         raise TdbemError(code, "tdbem_tc_gemm_check")
     return c
+
+
+def tdbem_eval_field(ctx, points, a0, na):
+    """Field u(x_p, t_a) at off-surface points for steps a0 .. a0+na-1:
+    [na, npts] float64."""
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((int(na), pts.shape[0]))
+    _check(ctx, lib().tdbem_eval_field(ctx, _ptr(pts), pts.shape[0], int(a0), int(na), _ptr(out)))
+    return out

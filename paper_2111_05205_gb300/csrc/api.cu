@@ -149,7 +149,7 @@ int tdbem_create(const tdbem_params *p, void *stream, tdbem_ctx **out)
     if (!p || !out) return TDBEM_ERR_ARG;
     *out = nullptr;
     if (!(p->c > 0) || !(p->dt > 0) || p->nt < 2 || p->d < 1 || p->d > kMaxD || (p->bie != 0 && p->bie != 1) ||
-        (p->algo != 0 && p->algo != 1) || p->precision < 0 || p->precision > 3)
+        (p->algo != 0 && p->algo != 1) || p->precision < 0 || p->precision > 3 || (p->precond != 0 && p->precond != 1))
         return TDBEM_ERR_ARG;
     c = new tdbem_ctx();
     c->P = *p;
@@ -942,6 +942,11 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->ms_m2l = c->ms[PH_M2L];
     o->launches_m2l = c->launches[PH_M2L];
     o->m2l_flops = c->m2l_flops;
+    o->ms_gemm = c->ms[PH_GEMM];
+    o->launches_gemm = c->launches[PH_GEMM];
+    o->gemm_tc_flops = c->gemm_tc_flops;
+    o->m2l_products = c->fmm.on ? (c->split ? c->fmm.nprod : 1) : 0;
+    o->launches_far_kernels = c->far_kernels;
     for (int l = 0; l < 11 && l < (int)c->fmm.lev.size(); ++l) o->m2l_tile_n[l] = c->fmm.lev[l].np ? c->fmm.lev[l].tile_n : 0;
     o->launches_far = c->launches[PH_FAR];
     o->fmm_lt = c->fmm.Lt;
@@ -975,6 +980,8 @@ int tdbem_reset_stats(tdbem_ctx *c)
     }
     c->steps_total = 0;
     c->m2l_flops = 0.0;
+    c->gemm_tc_flops = 0.0;
+    c->far_kernels = 0;
     return TDBEM_OK;
 }
 

@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
@@ -138,10 +139,10 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
 //   U(x_a, y_b, t_m, s_n) = (c (t_m - s_n) - r)_+^d / r,
 //   U^(p) = C(d, p) (c (t_m - s_n) - r)_+^(d-p) / r,
 // x_a - y_b = -offset s + ho w_a - hs w_b, t_m - s_n = l T dt + dt + ht (w_m - w_n).
-__global__ void k_m2l_operators(int ps, int pt, int d, int mu, double s, double hs, double ho, double T_dt, double dt,
+__global__ void k_m2l_operators(int ps, int pt, int d, int mu, int nblk, double s, double hs, double ho, double T_dt, double dt,
                                 double ht, double c, int noff, const int32_t *__restrict__ offs, double *op)
 {
-    const int P3 = ps * ps * ps, P = P3 * pt, nblk = mu + 1 + d;
+    const int P3 = ps * ps * ps, P = P3 * pt;
     int64_t total = (int64_t)noff * nblk * P * P;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -543,6 +544,312 @@ __global__ void k_m2l_reduce(int nc, int P3, int P, int nblk, int mu, int nslot,
     }
 }
 
+// Distance powers between the nodes of a canonical offset's observation and
+// source boxes: kr[c][e][a][b] = r_ab^(e-1) (e = 0: 1/r), e = 0..d-1 (the
+// slot e = 1, r^0 = 1, is not read), r_ab = |-c s + ho w_a - hs w_b|.
+template <typename T>
+__global__ void k_dist_powers(int ncls, int ps, int d, double s, double hs, double ho, const int32_t *__restrict__ codes,
+                              T *out)
+{
+    const int P3 = ps * ps * ps;
+    const int64_t n = (int64_t)ncls * d * P3 * P3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e % P3), a = (int)((e / P3) % P3);
+        const int ex = (int)((e / ((int64_t)P3 * P3)) % d), c = (int)(e / ((int64_t)P3 * P3 * d));
+        const int o = codes[c];
+        const int dx = o % 7 - 3, dy = (o / 7) % 7 - 3, dz = o / 49 - 3;
+        const int a1 = a % ps, a2 = (a / ps) % ps, a3 = a / (ps * ps);
+        const int b1 = b % ps, b2 = (b / ps) % ps, b3 = b / (ps * ps);
+        const double rx = -dx * s + ho * cheb_node(ps, a1) - hs * cheb_node(ps, b1);
+        const double ry = -dy * s + ho * cheb_node(ps, a2) - hs * cheb_node(ps, b2);
+        const double rz = -dz * s + ho * cheb_node(ps, a3) - hs * cheb_node(ps, b3);
+        const double r = sqrt(rx * rx + ry * ry + rz * rz);
+        double v = 1.0 / r;
+        for (int k = 0; k < ex; ++k) v *= r;
+        if constexpr (std::is_same<T, double>::value) {
+            out[e] = v;
+        } else {
+            const float hi = (float)v;
+            out[e] = make_float2(hi, (float)(v - (double)hi));
+        }
+    }
+}
+
+// Double-float (a float pair, ~48 bits) arithmetic: acc += x y by the exact
+// FMA two-product of the leading parts and the two-sum of Knuth; df_add
+// adds two double-float numbers.
+__device__ __forceinline__ void df_fma(float2 &acc, float2 x, float2 y)
+{
+    const float p = x.x * y.x;
+    const float pe = fmaf(x.x, y.x, -p) + (x.x * y.y + x.y * y.x);
+    const float s = acc.x + p;
+    const float bb = s - acc.x;
+    const float e = (acc.x - (s - bb)) + (p - bb);
+    const float lo = acc.y + pe + e;
+    acc.x = s + lo;
+    acc.y = lo - (acc.x - s);
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb) + a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
+template <typename T>
+__device__ __forceinline__ void gen_fma(T &acc, T x, T y)
+{
+    if constexpr (std::is_same<T, double>::value) acc = fma(x, y, acc);
+    else df_fma(acc, x, y);
+}
+
+template <typename T>
+__device__ __forceinline__ T gen_add(T a, T b)
+{
+    if constexpr (std::is_same<T, double>::value) return a + b;
+    else return df_add(a, b);
+}
+
+template <typename T>
+__device__ __forceinline__ T gen_shfl(T v, int o)
+{
+    if constexpr (std::is_same<T, double>::value) return __shfl_xor_sync(0xffffffffu, v, o);
+    else return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+template <typename T>
+__device__ __forceinline__ double gen_val(T v)
+{
+    if constexpr (std::is_same<T, double>::value) return v;
+    else return (double)v.x + (double)v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ T gen_from(double v)
+{
+    if constexpr (std::is_same<T, double>::value) {
+        return v;
+    } else {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+// The derivative contributions G_p (p = 1..d) of one level's M2L (the
+// U^(p) of Eq. U_expand at I_{k+mu+1}, applied to the moments of every
+// interaction pair of a cell), from the binomial expansion of
+// U^(p) = C(d,p) z^q / r, q = d - p, z = A + c ht w_m - c ht w_n - r,
+// A = c ((mu+1) T + 1) dt:
+//   G_p[a, m] = C(d,p) sum_{i+j+k=q} q!/(i! j! k!) (c ht w_m)^i (-c ht)^j
+//               sum_{e<=k} C(k,e) A^(k-e) (-1)^e F_{e,j}[a],
+//   F_{e,j}[a] = sum_pairs sum_b r_ab^(e-1) mu_j[b],  mu_j[b] = sum_n w_n^j M[b, n]
+// (the pair's moment, node indices permuted by its symmetry element).  So
+// the derivative rows need spatial products only (e + j <= d - 1; e = 1 is
+// a plain sum) instead of d P x P operator blocks per pair; they are summed
+// in FP64 (FP64 form) or double-float (tensor-core forms), since the
+// distant-future recurrence amplifies their rounding with the square of the
+// number of intervals.  One CTA per observation cell; per pair, one warp
+// per observation node at a time, its lanes striding the source nodes.
+// Kernel 1: time moments of every GEMM column (pair), node indices
+// permuted by the column's symmetry element:
+//   mu[col][j][b] = sum_n w_n^j M_S[g(b) + P3 n],  ssum[col][j] = sum_b mu[col][j][b].
+template <typename T, int D>
+__global__ void k_deriv_moments(int64_t np, int P3, int pt, const int32_t *__restrict__ pS,
+                                const uint8_t *__restrict__ pg, const int16_t *__restrict__ perm,
+                                const double *__restrict__ wt, const double *__restrict__ M, T *mu, double *ssum)
+{
+    const int64_t col = blockIdx.x;
+    const int P = P3 * pt;
+    const int Sc = pS[col], g = pg[col];
+    double wn[kMaxP];
+#pragma unroll
+    for (int n = 0; n < kMaxP; ++n) wn[n] = n < pt ? wt[n] : 0.0;
+    double part[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) part[j] = 0.0;
+    for (int b = threadIdx.x; b < P3; b += blockDim.x) {
+        const double *m = M + (int64_t)Sc * P + perm[g * P3 + b];
+        double w[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) w[j] = 0.0;
+        for (int n = 0; n < pt; ++n) {
+            const double x = m[(int64_t)P3 * n];
+            double pw = 1.0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                w[j] += pw * x;
+                pw *= wn[n];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const T v = gen_from<T>(w[j]);
+            mu[(col * D + j) * P3 + b] = v;
+            part[j] += gen_val(v);
+        }
+    }
+    __shared__ double red[D][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        double v = part[j];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        ssum[col * D + threadIdx.x] = v;
+    }
+}
+
+// Kernel 2: per symmetry class, the distance-power matrices times the
+// columns' time moments, in FP64 or double-float on the CUDA cores:
+//   Fp[col][e][j][a] = sum_b r_ab^(e-1) mu[col][j][b]  (e != 1, e + j <= D - 1),
+// a in the canonical node order.  One CTA per (class, 8 columns), one
+// thread per row a; the matrices go through shared memory 32 columns at a
+// time (rows padded to 33 entries), so each chunk serves 8 columns.
+constexpr int kDerivCols = 8;
+
+template <typename T, int D>
+__global__ void k_deriv_products(int P3, const int4 *__restrict__ jobs, const T *__restrict__ kr,
+                                 const T *__restrict__ mu, T *Fp)
+{
+    extern __shared__ double shm_d[];
+    T *mus = reinterpret_cast<T *>(shm_d);    // [kDerivCols][D][P3]
+    T *kc = mus + kDerivCols * D * P3;        // [P3][33]
+    const int4 job = jobs[blockIdx.x];        // class, first column, columns
+    const int cls = job.x, ncol = job.z;
+    const int64_t col0 = job.y;
+    const int r = threadIdx.x;
+    for (int x = threadIdx.x; x < kDerivCols * D * P3; x += blockDim.x) {
+        const int t = x / (D * P3);
+        mus[x] = t < ncol ? mu[col0 * D * P3 + x] : gen_from<T>(0.0);
+    }
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        if (e == 1) continue;
+        T acc[kDerivCols][D];
+#pragma unroll
+        for (int t = 0; t < kDerivCols; ++t)
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc[t][j] = gen_from<T>(0.0);
+        const T *K = kr + ((int64_t)cls * D + e) * P3 * P3;
+        for (int b0 = 0; b0 < P3; b0 += 32) {
+            __syncthreads();
+            for (int x = threadIdx.x; x < P3 * 32; x += blockDim.x) {
+                const int row = x >> 5, cc = x & 31;
+                kc[row * 33 + cc] = (b0 + cc < P3) ? K[(int64_t)row * P3 + b0 + cc] : gen_from<T>(0.0);
+            }
+            __syncthreads();
+            if (r < P3) {
+                const int nb = min(32, P3 - b0);
+                for (int cc = 0; cc < nb; ++cc) {
+                    const T x = kc[r * 33 + cc];
+#pragma unroll
+                    for (int t = 0; t < kDerivCols; ++t)
+#pragma unroll
+                        for (int j = 0; j + e < D; ++j) gen_fma(acc[t][j], x, mus[(t * D + j) * P3 + b0 + cc]);
+                }
+            }
+        }
+        if (r < P3)
+#pragma unroll
+            for (int t = 0; t < kDerivCols; ++t)
+                if (t < ncol)
+#pragma unroll
+                    for (int j = 0; j + e < D; ++j)
+                        Fp[(((col0 + t) * D + e) * D + j) * P3 + r] = acc[t][j];
+    }
+}
+
+// Kernel 3: per observation cell, F_{e,j}[a'] = sum over its pairs (list
+// order) of Fp[col][e][j][g^-1(a')], and S_j = sum of ssum; then
+// G_p[a', m] = sum_{e,j} coef[p-1][m][e][j] F_{e,j}[a'] (F_{1,j} = S_j), with
+// the binomial-expansion coefficients of Eq. U_expand tabulated per level
+// at setup (deriv_coef_table).
+template <typename T, int D>
+__global__ void k_deriv_assemble(int nc, int P3, int pt, const int64_t *__restrict__ ooff,
+                                 const int64_t *__restrict__ oidx, const uint8_t *__restrict__ og,
+                                 const int16_t *__restrict__ iperm, const T *__restrict__ Fp,
+                                 const double *__restrict__ ssum, const double *__restrict__ coef, double *G)
+{
+    const int O = blockIdx.x;
+    const int P = P3 * pt;
+    const int64_t t0 = ooff[O], t1 = ooff[O + 1];
+    __shared__ double S[D];
+    if (threadIdx.x < D) {
+        double v = 0.0;
+        for (int64_t t = t0; t < t1; ++t) v += ssum[oidx[t] * D + threadIdx.x];
+        S[threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < P3; r += blockDim.x) {
+        T F[D][D];
+#pragma unroll
+        for (int e = 0; e < D; ++e)
+#pragma unroll
+            for (int j = 0; j < D; ++j) F[e][j] = gen_from<T>(0.0);
+        for (int64_t t = t0; t < t1; ++t) {
+            const int64_t col = oidx[t];
+            const int a = iperm[og[t] * P3 + r];
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                if (e == 1) continue;
+#pragma unroll
+                for (int j = 0; j + e < D; ++j) F[e][j] = gen_add(F[e][j], Fp[((col * D + e) * D + j) * P3 + a]);
+            }
+        }
+        double Fv[D][D];
+#pragma unroll
+        for (int e = 0; e < D; ++e)
+#pragma unroll
+            for (int j = 0; j < D; ++j) Fv[e][j] = (e == 1) ? S[j] : gen_val(F[e][j]);
+        for (int p = 0; p < D; ++p)
+            for (int m = 0; m < pt; ++m) {
+                const double *cf = coef + ((int64_t)p * pt + m) * D * D;
+                double v = 0.0;
+#pragma unroll
+                for (int e = 0; e < D; ++e)
+#pragma unroll
+                    for (int j = 0; j + e < D; ++j) v += cf[e * D + j] * Fv[e][j];
+                G[((int64_t)p * nc + O) * P + r + (int64_t)P3 * m] = v;
+            }
+    }
+}
+
+template <typename T, int D>
+static cudaError_t launch_deriv_d(int nc, int P3, int pt, const FmmLevel &V, const double *wt,
+                                  const int16_t *perm, const int16_t *iperm, cudaStream_t s)
+{
+    T *mu = reinterpret_cast<T *>(V.dmu), *Fp = reinterpret_cast<T *>(V.dF);
+    const int bdim = std::max(128, (P3 + 31) / 32 * 32);
+    k_deriv_moments<T, D><<<(unsigned)V.np, 128, 0, s>>>(V.np, P3, pt, V.pS, V.pg, perm, wt, V.M, mu, V.dss);
+    const size_t shm = ((size_t)kDerivCols * D * P3 + (size_t)P3 * 33) * sizeof(T);
+    if (shm > 48 * 1024)
+        cudaFuncSetAttribute(k_deriv_products<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_deriv_products<T, D><<<V.njobs, bdim, shm, s>>>(P3, V.djobs, reinterpret_cast<const T *>(V.kr), mu, Fp);
+    k_deriv_assemble<T, D><<<nc, 256, 0, s>>>(nc, P3, pt, V.ooff, V.oidx, V.og, iperm, Fp, V.dss, V.dcoef, V.G);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_deriv(int d, int nc, int P3, int pt, const FmmLevel &V, const double *wt,
+                                const int16_t *perm, const int16_t *iperm, cudaStream_t s)
+{
+    switch (d) {
+    case 1: return launch_deriv_d<T, 1>(nc, P3, pt, V, wt, perm, iperm, s);
+    case 2: return launch_deriv_d<T, 2>(nc, P3, pt, V, wt, perm, iperm, s);
+    case 3: return launch_deriv_d<T, 3>(nc, P3, pt, V, wt, perm, iperm, s);
+    default: return launch_deriv_d<T, 4>(nc, P3, pt, V, wt, perm, iperm, s);
+    }
+}
+
+
 namespace {
 
 double h_cheb(int p, int a) { return cos((2.0 * a + 1.0) * M_PI / (2.0 * p)); }
@@ -673,7 +980,7 @@ static std::vector<TcTile> m2l_tiles(const Fmm &F, const FmmLevel &V, int bn, co
             const int r1 = std::min(F.R, r0 + kTcBM);
             bool zero = true;
             for (int blk = r0 / F.P; blk <= (r1 - 1) / F.P; ++blk)
-                if (bm[(size_t)ci * F.nblk + blk] != 0.0) zero = false;
+                if (bm[(size_t)ci * F.ngb + blk] != 0.0) zero = false;
             if (zero) continue;  // these rows of the products stay zero
             fl += 2.0 * (r1 - r0) * F.P * (double)n;
             for (int64_t j0 = 0; j0 < n; j0 += bn)
@@ -724,6 +1031,37 @@ static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V)
         }
     }
     return cudaSuccess;
+}
+
+// Coefficients of the derivative rows (Eq. U_expand expanded binomially in
+// the time nodes): U^(p) = C(d,p) z^q / r, q = d - p, z = A + cht w_m - cht w_n
+// - r, A = c ((mu+1) T + 1) dt, cht = c T dt / 2, gives
+// G_p[a,m] = sum_{e,j} coef[p-1][m][e][j] F_{e,j}[a] with F_{e,j}[a] =
+// sum_b r_ab^(e-1) sum_n w_n^j M[b,n] and
+// coef = C(d,p) sum_{i+j+k=q, k>=e} C(q,i) C(q-i,j) (cht w_m)^i (-cht)^j C(k,e) A^(k-e) (-1)^e.
+static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht)
+{
+    auto binom = [](int n, int k) {
+        double v = 1.0;
+        for (int i = 0; i < k; ++i) v = v * (n - i) / (i + 1);
+        return v;
+    };
+    std::vector<double> t((size_t)d * pt * d * d, 0.0);
+    for (int p = 1; p <= d; ++p) {
+        const int q = d - p;
+        for (int m = 0; m < pt; ++m) {
+            const double wm = h_cheb(pt, m);
+            for (int i = 0; i <= q; ++i)
+                for (int j = 0; i + j <= q; ++j) {
+                    const int k = q - i - j;
+                    for (int e = 0; e <= k; ++e)
+                        t[(((size_t)(p - 1) * pt + m) * d + e) * d + j] +=
+                            binom(d, p) * binom(q, i) * binom(q - i, j) * std::pow(cht * wm, i) * std::pow(-cht, j) *
+                            binom(k, e) * std::pow(A, k - e) * ((e & 1) ? -1.0 : 1.0);
+                }
+        }
+    }
+    return t;
 }
 
 // Tile-width tuner of the tensor-core M2L (the level's classes, column
@@ -836,7 +1174,8 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     F.nd = d * (d - 1) / 2;
     F.nslot = F.mu + 2;
     const int P = F.P, P3 = F.P3, ps = F.ps, pt = F.pt;
-    F.R = F.nblk * P;
+    F.ngb = F.mu + 1;  // operator blocks applied as GEMMs: the near future
+    F.R = F.ngb * P;
     F.Rp = (F.R + kTcBM - 1) / kTcBM * kTcBM;
     F.Kp = (P + kTcBK - 1) / kTcBK * kTcBK;
     if (!c->split) {
@@ -921,6 +1260,12 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             for (int np_ = 0; np_ < pt; ++np_) tm[h * pt * pt + np_ * pt + n] = v[np_];
         }
     F_TRY(falloc(c, &F.Tm, tm.size()));
+    {
+        std::vector<double> wt(pt);
+        for (int n = 0; n < pt; ++n) wt[n] = h_cheb(pt, n);
+        F_TRY(falloc(c, &F.wt, wt.size()));
+        F_TRY(cudaMemcpyAsync(F.wt, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    }
     F_TRY(cudaMemcpyAsync(F.Tm, tm.data(), tm.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
     F_TRY(falloc(c, &F.cmp, 16));
     F_TRY(falloc(c, &F.far, (size_t)F.Lt * ns));
@@ -993,7 +1338,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             for (int ci = 0; ci < V.ncls; ++ci) V.cbase[ci + 1] += V.cbase[ci];
             std::vector<int64_t> fill(V.cbase.begin(), V.cbase.end() - 1), ooff(V.nc + 1, 0), oidx(V.np);
             std::vector<int32_t> hS(V.np);
-            std::vector<uint8_t> hg(V.np), og(V.np);
+            std::vector<uint8_t> hg(V.np), og(V.np), hc(V.np);
             int64_t q = 0;
             for (int O = 0; O < V.nc; ++O) {
                 ooff[O + 1] = ooff[O] + cnt[O];
@@ -1001,6 +1346,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                     const int64_t col = fill[cls_of[pcls[q]]]++;
                     hS[col] = il[(size_t)O * 189 + t];
                     hg[col] = (uint8_t)pgrp[q];
+                    hc[col] = (uint8_t)cls_of[pcls[q]];
                     oidx[q] = col;
                     og[q] = (uint8_t)pgrp[q];
                 }
@@ -1010,6 +1356,8 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             F_TRY(falloc(c, &V.ooff, (size_t)V.nc + 1));
             F_TRY(falloc(c, &V.oidx, (size_t)V.np));
             F_TRY(falloc(c, &V.og, (size_t)V.np));
+            F_TRY(falloc(c, &V.pc, (size_t)V.np));
+            F_TRY(cudaMemcpyAsync(V.pc, hc.data(), V.np, cudaMemcpyHostToDevice, c->s));
             F_TRY(cudaMemcpyAsync(V.pS, hS.data(), V.np * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
             F_TRY(cudaMemcpyAsync(V.pg, hg.data(), V.np, cudaMemcpyHostToDevice, c->s));
             F_TRY(cudaMemcpyAsync(V.ooff, ooff.data(), (V.nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
@@ -1027,9 +1375,42 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             F_TRY(falloc(c, &op, nop));
             F_TRY(falloc(c, &d_codes, (size_t)V.ncls));
             F_TRY(cudaMemcpyAsync(d_codes, codes.data(), V.ncls * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
-            k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, V.s, V.hs, V.ho, Tdt, c->P.dt, Tdt / 2.0,
+            k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, F.ngb, V.s, V.hs, V.ho, Tdt, c->P.dt, Tdt / 2.0,
                                                         c->P.c, V.ncls, d_codes, op);
             F_TRY(cudaGetLastError());
+            // distance powers of the derivative rows (Eq. U_expand)
+            const size_t nkr = (size_t)V.ncls * d * P3 * P3;
+            if (c->split) {
+                float2 *kr = nullptr;
+                F_TRY(falloc(c, &kr, nkr));
+                k_dist_powers<float2><<<152 * 8, 256, 0, c->s>>>(V.ncls, ps, d, V.s, V.hs, V.ho, d_codes, kr);
+                V.kr = kr;
+            } else {
+                double *kr = nullptr;
+                F_TRY(falloc(c, &kr, nkr));
+                k_dist_powers<double><<<152 * 8, 256, 0, c->s>>>(V.ncls, ps, d, V.s, V.hs, V.ho, d_codes, kr);
+                V.kr = kr;
+            }
+            F_TRY(cudaGetLastError());
+            V.flops_deriv = 2.0 * P3 * P3 * (double)V.np * (d * (d + 1) / 2 - (d >= 2 ? d - 1 : 0));
+            {
+                // work of the derivative rows: buffers and (class, 8-column) jobs
+                const size_t el = c->split ? sizeof(float2) : sizeof(double);
+                F_TRY(falloc(c, (char **)&V.dmu, (size_t)V.np * d * P3 * el));
+                F_TRY(falloc(c, (char **)&V.dF, (size_t)V.np * d * d * P3 * el));
+                F_TRY(falloc(c, &V.dss, (size_t)V.np * d));
+                std::vector<int4> jobs;
+                for (int ci = 0; ci < V.ncls; ++ci)
+                    for (int64_t c0 = V.cbase[ci]; c0 < V.cbase[ci + 1]; c0 += kDerivCols)
+                        jobs.push_back(make_int4(ci, (int)c0, (int)std::min<int64_t>(kDerivCols, V.cbase[ci + 1] - c0), 0));
+                V.njobs = (int)jobs.size();
+                const double A = c->P.c * ((F.mu + 1) * Tdt + c->P.dt), cht = c->P.c * Tdt / 2.0;
+                std::vector<double> tab = deriv_coef_table(d, pt, A, cht);
+                F_TRY(falloc(c, &V.dcoef, tab.size()));
+                F_TRY(cudaMemcpyAsync(V.dcoef, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+                F_TRY(falloc(c, &V.djobs, std::max<size_t>(jobs.size(), 1)));
+                F_TRY(cudaMemcpyAsync(V.djobs, jobs.data(), jobs.size() * sizeof(int4), cudaMemcpyHostToDevice, c->s));
+            }
             if (!c->split) {
                 V.op = op;
                 F_TRY(falloc(c, &V.Bbuf, (size_t)V.np * P));
@@ -1041,10 +1422,10 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                 k_split_operators<<<152 * 32, 256, 0, c->s>>>(V.ncls, F.R, P, F.Rp, F.Kp, F.nta, op, V.opt);
                 F_TRY(cudaGetLastError());
                 double *d_bm = nullptr;
-                F_TRY(falloc(c, &d_bm, (size_t)V.ncls * F.nblk));
-                k_block_maxabs<<<V.ncls * F.nblk, 256, 0, c->s>>>(P, F.nblk, op, d_bm);
+                F_TRY(falloc(c, &d_bm, (size_t)V.ncls * F.ngb));
+                k_block_maxabs<<<V.ncls * F.ngb, 256, 0, c->s>>>(P, F.ngb, op, d_bm);
                 F_TRY(cudaGetLastError());
-                std::vector<double> bm((size_t)V.ncls * F.nblk);
+                std::vector<double> bm((size_t)V.ncls * F.ngb);
                 F_TRY(cudaMemcpyAsync(bm.data(), d_bm, bm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
                 F_TRY(cudaStreamSynchronize(c->s));
                 for (void *p : {(void *)op, (void *)d_bm}) {
@@ -1072,6 +1453,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
     cudaStream_t s = c->s;
     const double pref = 1.0 / (4.0 * M_PI * pow(c->cdt, d));
     const TreeLevel &TL = c->tree.levels[L];
+    ++c->far_kernels;
     k_p2m<<<TL.nc, 128, 0, s>>>(F.P3, P, F.Lt, k, d, c->ns, c->P.nt - 2, TL.cstart, c->tree.perm, F.At, F.As, c->d_q,
                                 c->d_u, F.wk, F.tl, pref, F.lev[L].M);
     F_TRY(cudaGetLastError());
@@ -1090,22 +1472,36 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
             phase_begin(c, &ev);
             const int64_t n = V.np * P;
             const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+            c->far_kernels += 3;  // gather, products, reduction
             if (c->split)
                 k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt);
             else
                 k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf);
             F_TRY(cudaGetLastError());
-            F_TRY(m2l_products(c, V));
+            {
+                cudaEvent_t eg;
+                phase_begin(c, &eg);
+                F_TRY(m2l_products(c, V));
+                phase_end(c, PH_GEMM, eg);
+                c->launches[PH_GEMM] += c->split ? 1 : V.ncls;
+                c->gemm_tc_flops += V.flops_app * (c->split ? F.nprod : 1);
+            }
             if (c->split)
-                k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx, V.og,
+                k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx, V.og,
                                                          F.iperm, V.C32, V.ring, V.G);
             else
-                k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.nblk, F.mu, F.nslot, kl, V.ooff, V.oidx,
+                k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx,
                                                           V.og, F.iperm, V.Cbuf, V.ring, V.G);
             F_TRY(cudaGetLastError());
+            // derivative contributions G (exact low-rank form of Eq. U_expand)
+            c->far_kernels += 3;
+            if (c->split)
+                F_TRY(launch_deriv<float2>(d, V.nc, F.P3, F.pt, V, F.wt, F.perm, F.iperm, s));
+            else
+                F_TRY(launch_deriv<double>(d, V.nc, F.P3, F.pt, V, F.wt, F.perm, F.iperm, s));
             phase_end(c, PH_M2L, ev);
             c->launches[PH_M2L] += 1;
-            c->m2l_flops += V.flops_app;
+            c->m2l_flops += V.flops_app + V.flops_deriv;
         } else {
             F_TRY(cudaMemsetAsync(V.G, 0, (size_t)d * V.nc * P * sizeof(double), s));
         }
@@ -1113,6 +1509,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
         cmp_table(d, kl, cm);
         F_TRY(cudaMemcpyAsync(F.cmp, cm, sizeof(cm), cudaMemcpyHostToDevice, s));
         int64_t n = (int64_t)V.nc * P;
+        ++c->far_kernels;
         k_m2l_recurrence<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
             n, d, F.mu, F.nslot, kl, V.G, V.D, V.A, V.ring, F.cmp, V.Tlen);
         F_TRY(cudaGetLastError());
@@ -1120,6 +1517,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
         if (l > 2) {
             FmmLevel &Pv = F.lev[l - 1];
             const TreeLevel &PT = c->tree.levels[l - 1];
+            ++c->far_kernels;
             k_m2m<<<Pv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, PT.ckey, V.nc, T.ckey, V.M, Pv.M, V.Sm, F.Tm, kl & 1);
             F_TRY(cudaGetLastError());
         }
@@ -1131,6 +1529,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
         if ((k + 1) % span) continue;
         int kc = (k + 1) / span, kp = kc / 2;
         FmmLevel &Pv = F.lev[l], &Cv = F.lev[l + 1];
+        ++c->far_kernels;
         k_l2l<<<Cv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, c->tree.levels[l].ckey, Cv.nc, c->tree.levels[l + 1].ckey,
                                       Pv.ring + (size_t)(kp % F.nslot) * Pv.nc * P,
                                       Cv.ring + (size_t)(kc % F.nslot) * Cv.nc * P, Cv.So, F.Tm, kc & 1);
@@ -1138,6 +1537,7 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k)
     }
     // L2P for observation interval k + 1
     FmmLevel &V = F.lev[L];
+    ++c->far_kernels;
     k_l2p<<<(int)(((int64_t)c->ns * 32 + 127) / 128), 128, 0, s>>>(c->ns, F.P3, F.pt, F.Lt, c->P.bie, c->P.c, c->tree.e2c,
                                               V.ring + (size_t)((k + 1) % F.nslot) * V.nc * P, F.Dv, F.Dn, F.tl,
                                               F.dtl, F.far);

@@ -443,6 +443,10 @@ int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_
 {
     if (!c || !S) return TDBEM_ERR_ARG;
     if (!c->prepared) return TDBEM_ERR_STATE;
+    if (c->P.precond == 0) {
+        c->err = "the context was created with precond = 0 (Jacobi only)";
+        return TDBEM_ERR_STATE;
+    }
     const int ns = c->ns, W = S->W, E = c->ell_w;
     double *mval = nullptr;
     int32_t *mcol = nullptr;

@@ -112,6 +112,15 @@ struct FmmLevel {
     std::vector<int64_t> cbase;  // [ncls+1] first column of each class
     int32_t *pS = nullptr;       // [np] source cell of each column
     uint8_t *pg = nullptr;       // [np] symmetry element of each column
+    uint8_t *pc = nullptr;       // [np] class of each column
+    void *kr = nullptr;          // [ncls][d][P3][P3] r_ab^(e-1) between the canonical nodes (e = 0..d-1;
+                                 // e = 1 unused): FP64, or float pairs in the tensor-core forms
+    void *dmu = nullptr;         // [np][d][P3] time moments of the columns (derivative rows)
+    void *dF = nullptr;          // [np][d][d][P3] their distance-power products
+    double *dss = nullptr;       // [np][d] sums of the time moments
+    int4 *djobs = nullptr;       // [njobs] (class, first column, columns) of the products kernel
+    double *dcoef = nullptr;     // [d][pt][d][d] binomial-expansion coefficients of the derivative rows
+    int njobs = 0;
     int64_t *ooff = nullptr;     // [nc+1] columns of each observation cell (CSR)
     int64_t *oidx = nullptr;     // [np] their columns, in interaction-list order
     uint8_t *og = nullptr;       // [np] their symmetry elements
@@ -127,14 +136,16 @@ struct FmmLevel {
     int tile_n = 128;            // tile width chosen by the setup-time tuner
     std::vector<std::pair<int, float>> tune;  // (tile width, ms) measured at setup
     CUtensorMap mapA{}, mapB{};
-    double flops_app = 0;        // algorithmic flops of one M2L application, 2 (mu+1+d) P^2 np
+    double flops_app = 0;        // algorithmic flops of one application's GEMMs: 2 P per kept operator row and pair
+    double flops_deriv = 0;      // and of its derivative rows: 2 P3^2 per spatial product and pair
 };
 
 struct Fmm {
     bool on = false;
     struct cublasContext *blas = nullptr;  // cuBLAS handle (FP64 form)
     int L = 0, ps = 0, pt = 0, P3 = 0, P = 0, mu = 0, Lt = 0, nblk = 0, nd = 0, nslot = 0;
-    int R = 0, Rp = 0, Kp = 0;              // operator rows, rows padded to 128, K padded to 64
+    int ngb = 0;                            // operator blocks applied as GEMMs (near future, mu + 1)
+    int R = 0, Rp = 0, Kp = 0;              // their rows ngb P, rows padded to 128, K padded to 64
     int nta = 0, ntb = 0, nprod = 0;        // tensor-core forms: split terms and products
     int prod[kTcMaxProd] = {0};
     int16_t *perm = nullptr;                // [48][P3] node permutation of each symmetry element
@@ -145,6 +156,7 @@ struct Fmm {
     double *tl = nullptr, *dtl = nullptr;  // [Lt][8] time basis at the interval's positions
     double *wk = nullptr;                   // [d+2] w^{kappa,d}
     double *Tm = nullptr;                   // [2][pt][pt] time transfer
+    double *wt = nullptr;                   // [pt] Chebyshev time nodes
     double *cmp = nullptr;                  // c_m^p(k) of the current call
     double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
     int far_k = -1;                         // leaf interval the far field belongs to
@@ -155,7 +167,7 @@ struct Pending {
     cudaEvent_t a, b;
 };
 
-enum { PH_RHS = 0, PH_NEAR = 1, PH_SOLVE = 2, PH_FAR = 3, PH_M2L = 4, PH_COUNT = 5 };
+enum { PH_RHS = 0, PH_NEAR = 1, PH_SOLVE = 2, PH_FAR = 3, PH_M2L = 4, PH_GEMM = 5, PH_COUNT = 6 };
 
 struct Status {
     int code = TDBEM_OK;
@@ -247,9 +259,11 @@ struct tdbem_ctx {
     // timing
     std::vector<tdbem::Pending> pending;
     std::vector<cudaEvent_t> pool;
-    double ms[tdbem::PH_COUNT] = {0, 0, 0, 0, 0};
-    int64_t launches[tdbem::PH_COUNT] = {0, 0, 0, 0, 0};
+    double ms[tdbem::PH_COUNT] = {0, 0, 0, 0, 0, 0};
+    int64_t launches[tdbem::PH_COUNT] = {0, 0, 0, 0, 0, 0};
     double m2l_flops = 0.0;  // algorithmic flops of the M2L GEMMs since the last reset
+    double gemm_tc_flops = 0.0;  // tensor-pipe flops the split requires (products x algorithmic)
+    int64_t far_kernels = 0;     // kernel launches of the far-field passes (FP64 form: DGEMMs count once)
     int64_t steps_total = 0;
     double ms_prepare = 0.0;
 };

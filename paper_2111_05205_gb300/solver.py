@@ -21,22 +21,26 @@ class Solver:
     ``fmm``: (ps, pt, mu) to evaluate the far part with the space-time FMM
     (needs ``depth`` >= 2; mu = 0 picks the smallest valid value).
     ``stream``: a cudaStream_t handle (int) or None.  ``precision``: 0 /
-    "fp64" or 1 / "split" (float-pair double-float history sum).
+    "fp64" or 1 / "split" (float-pair double-float history sum; FMM M2L with
+    BF16 x 3 terms), 2 / "bf16x3", 3 / "bf16" (cheaper M2L products).
+    ``precond``: 0 Jacobi zero-lag solve, 1 allow a learned SAI
+    (tdbem_set_precond).
     """
 
     def __init__(self, xyz, tri, c, dt, nt, d, bie, phi=None, known=None, incident=None, stream=None,
-                 solver_tol=0.0, solver_maxit=0, precision=0, depth=0, fmm=None):
+                 solver_tol=0.0, solver_maxit=0, precision=0, depth=0, fmm=None, precond=0):
         p = abi.tdbem_params()
         p.c, p.dt, p.nt, p.d = float(c), float(dt), int(nt), int(d)
         p.bie = {"obie": 0, "bmbie": 1}[bie] if isinstance(bie, str) else int(bie)
         p.algo = 0
-        p.precision = {"fp64": 0, "split": 1}.get(precision, precision)
+        p.precision = {"fp64": 0, "split": 1, "bf16x3": 2, "bf16": 3}.get(precision, precision)
         p.depth = int(depth)
         if fmm is not None:  # (ps, pt, mu): the space-time FMM for the far part
             p.algo = 1
             p.ps, p.pt, p.mu = (int(v) for v in fmm)
         p.solver_tol = float(solver_tol)
         p.solver_maxit = int(solver_maxit)
+        p.precond = int(precond)
         self.ns = int(np.asarray(tri).shape[0])
         self.nt = int(nt)
         self.ctx = abi.tdbem_create(p, stream)

@@ -97,11 +97,11 @@ def workload(name, nt=None):
         # e.g. paper_sphere2880_bmbie_d2_hard
         parts = name.split("_")
         ns = int(parts[1][len("sphere"):])
-        n, dt, nt = {2880: (12, 0.04, 240), 5120: (16, 0.03, 320), 11520: (24, 0.02, 480),
-                     80: (2, 0.25, 40), 320: (4, 0.12, 80)}[ns]
+        n, dt, steps = {2880: (12, 0.04, 240), 5120: (16, 0.03, 320), 11520: (24, 0.02, 480),
+                        80: (2, 0.25, 40), 320: (4, 0.12, 80)}[ns]
         xyz, tri = geodesic(n, radius=0.5, center=(0.5, 0.0, 0.0))
         bc = {"hard": "neumann", "soft": "dirichlet"}[parts[4]]
-        w = Workload(name, xyz, tri, c, dt, nt, int(parts[3][1:]), parts[2], bc, "plane", sigma=0.5, t0=0.0,
+        w = Workload(name, xyz, tri, c, dt, steps, int(parts[3][1:]), parts[2], bc, "plane", sigma=0.5, t0=0.0,
                      direction=np.array([1.0, 0.0, 0.0]), shape=1)
     elif name.startswith("ellipsoid") and "_plane" in name:
         # small seeded ellipsoids for tests, e.g. ellipsoid320_bmbie_d2_hard_plane_s7

@@ -21,12 +21,12 @@ def phi_of(w):
     return np.full(w.ns, 1 if w.bc == "neumann" else 0, dtype=np.int8)
 
 
-def gpu_solver(w, stream=None, precision=0, depth=0, fmm=None):
+def gpu_solver(w, stream=None, precision=0, depth=0, fmm=None, precond=0):
     from paper_2111_05205_gb300 import Solver
     inc = (w.direction, w.t0, w.sigma, w.shape) if w.excitation == "plane" else None
     known = known_samples(w) if w.excitation == "uniform" else None
     return Solver(w.xyz, w.tri, w.c, w.dt, w.nt, w.d, w.bie, phi=phi_of(w), known=known, incident=inc,
-                  stream=stream, precision=precision, depth=depth, fmm=fmm)
+                  stream=stream, precision=precision, depth=depth, fmm=fmm, precond=precond)
 
 
 def gpu_march(w, precision=0):

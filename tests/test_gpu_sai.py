@@ -59,9 +59,12 @@ def test_learned_sai_beats_jacobi_on_a_held_out_mesh():
     sai = abi.tdbem_sai_create(12, 32, 3)
     try:
         w = workload("ellipsoid1280_bmbie_d2_hard_plane_s99", nt=30)
-        a, b, c0 = gpu_solver(w), gpu_solver(w), gpu_solver(w)
+        a, b, c0 = gpu_solver(w), gpu_solver(w, precond=1), gpu_solver(w, precond=1)
         try:
             kj = a.stats()["solve_iters"]
+            with pytest.raises(abi.TdbemError) as e:  # precond = 0: Jacobi only
+                abi.tdbem_set_precond(a.ctx, sai)
+            assert e.value.code == -8
             use0, sweeps0, q0 = abi.tdbem_set_precond(c0.ctx, sai)  # untrained: the analytic part
             L0 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 1, 0.0)
             L1 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 150, 2e-3)
