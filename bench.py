@@ -734,12 +734,15 @@ def run_reference(args):
 
 def run_batch(args):
     """Batched driver on a mix shaped like the batched workload: N independent
-    instances (seeded ellipsoids; Ns alternating 1280 / 5120; Nt drawn from
-    U{256..1024}; OBIE d=1 and BMBIE d=2 alternating; sound-hard; split
-    precision).  From the same start (a checkpoint after the warm-up steps)
-    every instance is marched to its own last step Nt-1 by (a) plain
-    launches, one instance after another, (b) one graph per instance, (c) one
-    graph for all instances, replayed until the longest is done (shorter ones
+    instances (seeded ellipsoids; Ns cycling 1280 / 5120 / 20480; Nt drawn
+    from U{256..1024}; OBIE d=1 and BMBIE d=2 alternating; sound-hard), every
+    one marched with the space-time FMM (ps = pt = 5, octree depth 2 / 3 / 4
+    by size, M2L on the tensor cores in the FP32-grade split; the tile width
+    of every level's GEMM picked by the setup-time tuner).  From the same
+    start (a checkpoint after the warm-up steps) every instance is marched to
+    its own last step Nt-1 by (a) plain launches, one instance after another,
+    (b) one graph per instance, (c) one batch graph for all instances holding
+    16 steps of each (graph launches until the longest is done; shorter ones
     stop at their end on the device).  Timed with the host clock around each
     mode, device synchronised."""
     import torch
@@ -750,11 +753,25 @@ def run_batch(args):
     n = args.batch
     rng = np.random.default_rng(2024)
     nts = [int(v) for v in rng.integers(256, 1025, size=n)]
-    ws = [workload("ellipsoid%d_%s_hard_plane_s%d" % ((1280, 5120)[i % 2], ("bmbie_d2", "obie_d1")[(i // 2) % 2], i + 1),
+    sizes = (1280, 5120, 20480)
+    depth_of = {1280: 2, 5120: 3, 20480: 4}
+    ws = [workload("ellipsoid%d_%s_hard_plane_s%d" % (sizes[i % 3], ("bmbie_d2", "obie_d1")[(i // 3) % 2], i + 1),
                    nt=nts[i]) for i in range(n)]
     t0 = time.time()
-    sols = [gpu_solver(w, precision=1) for w in ws]
+    sols, depths = [], []
+    for w in ws:
+        # the deepest feasible octree up to the size's depth (leaf cells
+        # larger than c dt and the element size)
+        for depth in range(depth_of[w.ns], 1, -1):
+            try:
+                sols.append(gpu_solver(w, precision=1, depth=depth, fmm=(5, 5, 0)))
+                depths.append(depth)
+                break
+            except abi.TdbemError as e:
+                if e.code != -7 or depth == 2:
+                    raise
     setup_s = time.time() - t0
+    spl = 16
     try:
         for s in sols:
             abi.tdbem_step(s.ctx, args.warmup)
@@ -774,14 +791,16 @@ def run_batch(args):
         torch.cuda.synchronize()
         t_plain = time.perf_counter() - t
         X_plain = [s.solution(0, nt - 1)[0] for s, nt in zip(sols, nts)]
+        st = [s.stats() for s in sols]
         reset()
         t = time.perf_counter()
         for s, m in zip(sols, todo):
             abi.tdbem_step_graph(s.ctx, m)
         torch.cuda.synchronize()
         t_graph = time.perf_counter() - t
+        same_graph = all(np.array_equal(s.solution(0, nt - 1)[0], x) for s, nt, x in zip(sols, nts, X_plain))
         reset()
-        B = abi.tdbem_batch_create([s.ctx for s in sols])
+        B = abi.tdbem_batch_create_steps([s.ctx for s in sols], spl)
         try:
             t = time.perf_counter()
             abi.tdbem_batch_step(B, max(todo))
@@ -790,20 +809,22 @@ def run_batch(args):
         finally:
             abi.tdbem_batch_destroy(B)
         same = all(np.array_equal(s.solution(0, nt - 1)[0], x) for s, nt, x in zip(sols, nts, X_plain))
-        launches = sum(m * (1 + s.stats()["solve_iters"] + 1) for s, m in zip(sols, todo))
+        launches = int(sum(x["launches_near"] + x["launches_solve"] + x["launches_far_kernels"] for x in st))
     finally:
         for s in sols:
             s.close()
     print(json.dumps({"metric": "instance-steps/sec, batched driver", "value": tot / t_batch,
                       "unit": "instance-steps/s", "n_gpus": 1, "steps": max(todo), "warmup": args.warmup,
-                      "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
-                      "config": {"workload": "batch%d_ellipsoids_ns1280-5120_nt256-1024_obie-d1_bmbie-d2" % n,
-                                 "instances": n, "ns": [w.ns for w in ws], "nt": nts,
-                                 "instance_steps": tot, "setup_s": round(setup_s, 1),
-                                 "excluded": "Ns=20480 instances: the direct form needs 15 GB of coefficients "
-                                             "each, and FMM steps are not graph-replayed"},
+                      "higher_is_better": True, "dtype": "f64+bf16", "data": "synthetic",
+                      "config": {"workload": "batch%d_ellipsoids_ns1280-5120-20480_nt256-1024_obie-d1_bmbie-d2_fmm_p5x5"
+                                             % n, "instances": n, "ns": [w.ns for w in ws], "nt": nts,
+                                 "depth": depths, "ps": 5, "pt": 5, "precision": PREC_TEXT[1],
+                                 "steps_per_graph_launch": spl, "instance_steps": tot,
+                                 "setup_s": round(setup_s, 1),
+                                 "m2l_tile_n": [x["m2l_tile_n"][:d + 1] for x, d in zip(st, depths)]},
                       "plain_launches": tot / t_plain, "graph_per_instance": tot / t_graph,
-                      "batch_equals_plain": bool(same), "gpu_launches_plain": int(launches),
+                      "batch_equals_plain": bool(same), "graph_equals_plain": bool(same_graph),
+                      "gpu_launches_plain": launches,
                       "timing": "host clock around each mode, device synchronised"}))
 
 
@@ -854,6 +875,83 @@ def run_stability(args):
                       "rows": rows}))
 
 
+def run_sai_study(args):
+    """The learned SAI of the zero-lag solve at scale: the network (12 slots,
+    32 hidden units, FP16 weights) is trained on the GPU, by the library's
+    own forward, backward and Adam kernels, on the zero-lag matrices the
+    library assembles for 200 seeded random ellipsoids (Ns cycling 1280 /
+    5120 / 20480; Burton-Miller, d = 2, sound-hard); then, on held-out
+    problems -- the 81920-element icosphere (subdivision 6, BMBIE d = 2
+    sound-hard under the plane pulse, Nt = 2048, FMM) and the 20480-element
+    benchmark ellipsoid -- the same march runs once with Jacobi and once
+    with the learned SAI installed (tdbem_set_precond), each timed over the
+    same steps with CUDA events; reported: sweeps and contraction of each
+    solver, the zero-lag solve's ms per step (phase time of the library) and
+    the whole step's, and the difference of the two histories (both solve
+    to 1e-16)."""
+    import torch
+    from paper_2111_05205_gb300 import abi, build
+    from synth import workload
+    from tests.gpu_cases import gpu_solver
+    build.build()
+    t0 = time.time()
+    sizes = (1280, 5120, 20480)
+    train = [gpu_solver(workload("ellipsoid%d_bmbie_d2_hard_plane_s%d" % (sizes[i % 3], 1000 + i), nt=2))
+             for i in range(args.sai_meshes)]
+    setup_s = time.time() - t0
+    sai = abi.tdbem_sai_create(12, 32, 3)
+    out = {"study": "learned SAI of the zero-lag solve against Jacobi (held-out meshes)",
+           "training": {"meshes": len(train), "ns": "cycling 1280/5120/20480", "epochs": args.sai_epochs,
+                        "setup_s": round(setup_s, 1)}}
+    try:
+        t0 = time.time()
+        L0 = abi.tdbem_sai_train(sai, [t.ctx for t in train], 1, 0.0)
+        L1 = abi.tdbem_sai_train(sai, [t.ctx for t in train], args.sai_epochs, 2e-3)
+        out["training"].update({"loss_before": L0, "loss_after": L1, "train_s": round(time.time() - t0, 1)})
+        for t in train:
+            t.close()
+        train = []
+        cases = [("sphere81920_bmbie_d2_hard_plane", 5, (4, 4, 0), 2048),
+                 ("ellipsoid20480_bmbie_d2_hard_plane", 3, (7, 7, 0), 1024)]
+        out["held_out"] = []
+        for name, depth, fmm, nt in cases:
+            w = workload(name, nt=nt)
+            row = {"workload": name, "ns": w.ns, "nt": nt, "depth": depth, "ps": fmm[0], "pt": fmm[1]}
+            res = {}
+            X = {}
+            for label, precond in (("jacobi", 0), ("learned_sai", 1)):
+                s = gpu_solver(w, precision=1, depth=depth, fmm=fmm, precond=precond)
+                try:
+                    if precond:
+                        use, sweeps, q = abi.tdbem_set_precond(s.ctx, sai)
+                        res["sai_installed"] = bool(use)
+                    st = s.stats()
+                    cyc = st["fmm_lt"] << max(depth - 2, 0)
+                    spin = cyc + 3
+                    n = max(cyc, (200 // cyc) * cyc)
+                    abi.tdbem_step(s.ctx, spin)
+                    abi.tdbem_sync(s.ctx)
+                    abi.tdbem_reset_stats(s.ctx)
+                    ms = _timed(abi, torch, s.ctx, n)
+                    st = s.stats()
+                    res[label] = {"sweeps": st["solve_iters"], "contraction": st["solve_contraction"],
+                                  "solve_ms_per_step": st["ms_solve"] / n, "step_ms": ms / n,
+                                  "solve_launches_per_step": st["launches_solve"] / n}
+                    s.step()
+                    X[label] = s.solution(0, nt - 1)[0]
+                finally:
+                    s.close()
+            res["rel_l2_sai_vs_jacobi"] = _rel(X["learned_sai"], X["jacobi"])
+            res["solve_speedup"] = res["jacobi"]["solve_ms_per_step"] / res["learned_sai"]["solve_ms_per_step"]
+            row.update(res)
+            out["held_out"].append(row)
+    finally:
+        for t in train:
+            t.close()
+        abi.tdbem_sai_destroy(sai)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -876,14 +974,19 @@ def main():
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
                     help="--algo fmm: skip the comparison runs against the direct path and the FP64 form")
     ap.add_argument("--batch", type=int, default=0, help="measure the batched driver with N instances")
-    ap.add_argument("--study", default="", choices=["", "stability"],
-                    help="stability: the sphere example of Section 5.1 for every BIE, d and boundary condition")
+    ap.add_argument("--study", default="", choices=["", "stability", "sai"],
+                    help="stability: the sphere example of Section 5.1 for every BIE, d and boundary condition; "
+                         "sai: the learned zero-lag preconditioner trained on 200 meshes, against Jacobi")
+    ap.add_argument("--sai-meshes", type=int, default=200)
+    ap.add_argument("--sai-epochs", type=int, default=60)
     ap.add_argument("--study-sizes", default="2880,5120,11520")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.study == "stability":
         run_stability(args)
+    elif args.study == "sai":
+        run_sai_study(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.batch:

@@ -101,8 +101,10 @@ typedef struct {
                                       block offsets (8 B per 32 pairs), the history window
                                       (gamma_max x ns x 8 B per history kind) and b */
     int32_t gamma_max;             /* largest lag stored */
-    int32_t solve_iters;           /* zero-lag iterations per step */
-    double solve_contraction;      /* max_i sum_{j!=i} |A_ij / A_ii| */
+    int32_t solve_iters;           /* zero-lag sweeps per step of the solver in use (Jacobi, or the
+                                      learned SAI once tdbem_set_precond installed it) */
+    double solve_contraction;      /* its contraction: max_i sum_{j!=i} |A_ij / A_ii| for Jacobi,
+                                      ||I - M A||_inf for the SAI */
     double ms_prepare;             /* wall time of tdbem_prepare */
     double ms_far;                 /* FMM: P2M..L2P at leaf-interval boundaries */
     int64_t launches_far;          /* FMM: boundaries processed */
@@ -185,14 +187,22 @@ int tdbem_step(tdbem_ctx *ctx, int32_t nsteps);
  * NULL. */
 int tdbem_step_io(tdbem_ctx *ctx, int32_t nsteps, const double *exc, double *x_out, int32_t on_device);
 
-/* Same as tdbem_step (direct path, algo 0) but every step is one replay of a
- * CUDA graph that holds the step's kernels (history sum, Jacobi sweeps and a
- * device-side step counter), captured at the first call: no per-kernel
- * launch cost.  Results are identical to tdbem_step.  ERR_ARG for algo 1. */
+/* Same as tdbem_step but every step is one replay of a CUDA graph that holds
+ * the step's kernels (history sum, Jacobi sweeps and a device-side step
+ * counter), captured at the first call: no per-kernel launch cost.  With the
+ * FMM (algo 1) the graph also holds every far-field pass of every level
+ * (Section 3: P2M, M2L, Formula 1, M2M, L2L, L2P); each of those kernels
+ * reads the step from the device counter and does its work only at the
+ * steps where plain stepping would run it (leaf-interval boundaries, and for
+ * level l every 2^(L-l)-th of them), so the graph is the same for every
+ * step.  Results are identical to tdbem_step (bit for bit).  ERR_ARG for
+ * the FP64 FMM form (precision 0: its GEMMs are library calls that cannot
+ * test the step) and with a learned SAI installed. */
 int tdbem_step_graph(tdbem_ctx *ctx, int32_t nsteps);
 
-/* Batched driver: several independent instances (contexts of the direct
- * path on one device, e.g. scatterers of different size, order and BIE)
+/* Batched driver: several independent instances (contexts on one device,
+ * direct path or FMM in a tensor-core precision, e.g. scatterers of
+ * different size, order and BIE)
  * advanced together, each step of all of them one replay of a single CUDA
  * graph in which every instance's step is an independent branch, so that
  * small instances share the GPU.  tdbem_batch_create captures the graph
@@ -207,6 +217,11 @@ int tdbem_step_graph(tdbem_ctx *ctx, int32_t nsteps);
  * are identical to stepping each context alone. */
 typedef struct tdbem_batch tdbem_batch;
 int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out);
+/* As tdbem_batch_create, and a second graph holds steps_per_launch
+ * (1..1024) consecutive steps of every instance, so that one graph launch
+ * advances the whole batch that many steps; tdbem_batch_step replays it as
+ * often as the requested steps allow and the one-step graph for the rest. */
+int tdbem_batch_create_steps(tdbem_ctx *const *ctxs, int32_t n, int32_t steps_per_launch, tdbem_batch **out);
 int tdbem_batch_step(tdbem_batch *batch, int32_t nsteps);
 int tdbem_batch_sync(tdbem_batch *batch);
 void tdbem_batch_destroy(tdbem_batch *batch);
@@ -264,9 +279,12 @@ int tdbem_sai_gradient(tdbem_sai *sai, tdbem_ctx *ctx, float *grad, float *loss)
  * floats) to inout, set = 1 loads inout (and resets the optimiser). */
 int tdbem_sai_weights(tdbem_sai *sai, float *inout, int64_t *count, int32_t set);
 /* Installs the network's M as the context's zero-lag solver (sweeps
- * x <- x + M (b - A x), one launch each, count from ||I - M A||_inf so that
- * the error stays below solver_tol) when that takes fewer sweeps than
- * Jacobi; otherwise Jacobi stays.  *use_sai, *sweeps, *contraction report the choice.
+ * x <- x + M (b - A x), all K of a step in one cooperative launch with a
+ * bounded grid barrier where the device supports it, else one launch each;
+ * K from ||I - M A||_inf so that the error stays below solver_tol) when that
+ * takes fewer sweeps than Jacobi; otherwise Jacobi stays.  *use_sai,
+ * *sweeps, *contraction report the choice (tdbem_get_stats then reports the
+ * SAI's sweeps and contraction as solve_iters / solve_contraction).
  * ERR_STATE for a context created with precond = 0 (Jacobi only) or not prepared. */
 int tdbem_set_precond(tdbem_ctx *ctx, const tdbem_sai *sai, int32_t *use_sai, int32_t *sweeps, double *contraction);
 

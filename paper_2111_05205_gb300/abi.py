@@ -78,6 +78,7 @@ SIGNATURES = {
     "tdbem_sai_weights": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _I]),
     "tdbem_set_precond": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdbem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "tdbem_batch_create_steps": (ctypes.c_int, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P)]),
     "tdbem_batch_step": (ctypes.c_int, [_P, _I]),
     "tdbem_batch_sync": (ctypes.c_int, [_P]),
     "tdbem_batch_destroy": (None, [_P]),
@@ -201,6 +202,15 @@ def tdbem_batch_create(ctxs):
     code = lib().tdbem_batch_create(arr, len(ctxs), ctypes.byref(out))
     if code != TDBEM_OK:
         raise TdbemError(code, "tdbem_batch_create")
+    return out.value
+
+
+def tdbem_batch_create_steps(ctxs, steps_per_launch):
+    arr = (_P * len(ctxs))(*ctxs)
+    out = _P()
+    code = lib().tdbem_batch_create_steps(arr, len(ctxs), int(steps_per_launch), ctypes.byref(out))
+    if code != TDBEM_OK:
+        raise TdbemError(code, "tdbem_batch_create_steps")
     return out.value
 
 

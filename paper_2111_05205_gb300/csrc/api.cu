@@ -134,6 +134,7 @@ int check_flags(tdbem_ctx *c)
         // solve with one launch per sweep from now on
         cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
         c->jac_grid = 0;
+        c->sai_grid = 0;
         return fail(c, TDBEM_ERR_TIMEOUT, "zero-lag solve: grid barrier timed out");
     }
     return TDBEM_OK;
@@ -505,7 +506,9 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
         c->launches[PH_NEAR] += 1;
         {
             PhaseTimer t(c, PH_SOLVE);
-            if (c->sai_val) {
+            if (c->sai_val && c->sai_grid > 0) {
+                TD_CUDA(launch_sai_fused(c, alpha));
+            } else if (c->sai_val) {
                 for (int it = 0; it < c->sai_iters; ++it) TD_CUDA(launch_sai_sweep(c, alpha, it));
             } else if (c->jac_grid > 0) {
                 TD_CUDA(launch_jacobi_fused(c, alpha));
@@ -514,7 +517,7 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
                     TD_CUDA(launch_jacobi(c, alpha, it, it == c->solve_iters - 1));
             }
         }
-        c->launches[PH_SOLVE] += c->sai_val ? c->sai_iters : (c->jac_grid > 0 ? 1 : c->solve_iters);
+        c->launches[PH_SOLVE] += c->sai_val ? (c->sai_grid > 0 ? 1 : c->sai_iters) : (c->jac_grid > 0 ? 1 : c->solve_iters);
         c->alpha = alpha;
         c->steps_total += 1;
     }
@@ -528,7 +531,12 @@ static cudaError_t launch_step_chain(tdbem_ctx *c, cudaStream_t st)
     cudaStream_t keep = c->s;
     c->s = st;
     c->alpha_dev_on = true;
-    cudaError_t e = launch_near_sum(c, 0, nullptr, nullptr);
+    cudaError_t e = cudaSuccess;
+    // FMM: every far-field pass, each deciding on the device whether this
+    // step is one of its boundaries (Section 3), then the near sum reading
+    // the far field of the step's position in its leaf interval
+    if (c->fmm.on) e = fmm_boundary(c, 0, true);
+    if (e == cudaSuccess) e = launch_near_sum(c, 0, nullptr, c->fmm.on ? c->fmm.far : nullptr);
     for (int it = 0; it < c->solve_iters && e == cudaSuccess; ++it) e = launch_jacobi(c, 0, it, it == c->solve_iters - 1);
     if (e == cudaSuccess) e = launch_alpha_next(c);
     c->alpha_dev_on = false;
@@ -536,10 +544,18 @@ static cudaError_t launch_step_chain(tdbem_ctx *c, cudaStream_t st)
     return e;
 }
 
+// After graph-replayed steps: the far field in the buffer is the one of the
+// leaf interval holding the last step (plain stepping resumes from there).
+static void graph_steps_done(tdbem_ctx *c)
+{
+    if (c->fmm.on && c->alpha >= 1) c->fmm.far_k = (c->alpha - 1) / c->fmm.Lt;
+}
+
 static int graph_ready(tdbem_ctx *c)
 {
     if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "graph step before prepare");
-    if (c->fmm.on) return fail(c, TDBEM_ERR_ARG, "graph-replayed steps are for the direct path (algo 0)");
+    if (c->fmm.on && !c->split)
+        return fail(c, TDBEM_ERR_ARG, "graph-replayed FMM steps need a tensor-core precision (1-3)");
     if (c->sai_val) return fail(c, TDBEM_ERR_ARG, "graph-replayed steps use the Jacobi zero-lag solve");
     if (!c->d_alpha) TD_CUDA(dalloc(c, &c->d_alpha, 1));
     return TDBEM_OK;
@@ -571,6 +587,7 @@ int tdbem_step_graph(tdbem_ctx *c, int32_t nsteps)
     c->launches[PH_SOLVE] += (int64_t)nsteps * c->solve_iters;
     c->alpha += nsteps;
     c->steps_total += nsteps;
+    graph_steps_done(c);
     TD_CUDA(join(c->s, c->user));
     return TDBEM_OK;
 }
@@ -963,8 +980,9 @@ int tdbem_get_stats(const tdbem_ctx *cc, tdbem_stats *o)
     o->near_bytes_per_step = c->ncoef * 8 * kinds + c->npairs * (c->d_col ? 6 : 2) + c->nbt * 8 +
                              (int64_t)c->gmax * c->ns * 8 * kinds + (int64_t)c->ns * 8;
     o->gamma_max = c->gmax;
-    o->solve_iters = c->solve_iters;
-    o->solve_contraction = c->contraction;
+    // the zero-lag solver in use: the learned SAI once installed, else Jacobi
+    o->solve_iters = c->sai_val ? c->sai_iters : c->solve_iters;
+    o->solve_contraction = c->sai_val ? c->sai_contraction : c->contraction;
     o->ms_prepare = c->ms_prepare;
     return TDBEM_OK;
 }
@@ -996,14 +1014,38 @@ int tdbem_sync(tdbem_ctx *c)
 struct tdbem_batch {
     std::vector<tdbem_ctx *> ctx;
     cudaStream_t s = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;   // one step of every instance
+    cudaGraphExec_t graphk = nullptr;  // k consecutive steps of every instance (k > 1)
+    int k = 1;
     std::vector<cudaEvent_t> ev;
     std::string err;
 };
 
-int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out)
+// Captures `steps` consecutive steps of every instance into one graph, each
+// instance an independent branch (fork from and join into B->s).
+static cudaError_t batch_capture(tdbem_batch *B, int steps, cudaGraphExec_t *out)
 {
-    if (!ctxs || n < 1 || !out) return TDBEM_ERR_ARG;
+    const int n = (int)B->ctx.size();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(B->ev[n], B->s);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        tdbem_ctx *c = B->ctx[k];
+        e = cudaStreamWaitEvent(c->s, B->ev[n], 0);
+        for (int t = 0; t < steps && e == cudaSuccess; ++t) e = launch_step_chain(c, c->s);
+        if (e == cudaSuccess) e = cudaEventRecord(B->ev[k], c->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->s, B->ev[k], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(B->s, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+int tdbem_batch_create_steps(tdbem_ctx *const *ctxs, int32_t n, int32_t steps_per_launch, tdbem_batch **out)
+{
+    if (!ctxs || n < 1 || !out || steps_per_launch < 1 || steps_per_launch > 1024) return TDBEM_ERR_ARG;
     *out = nullptr;
     int dev = ctxs[0] ? ctxs[0]->dev : -1;
     for (int k = 0; k < n; ++k) {
@@ -1016,31 +1058,24 @@ int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out)
     }
     tdbem_batch *B = new tdbem_batch();
     B->ctx.assign(ctxs, ctxs + n);
+    B->k = steps_per_launch;
     cudaError_t e = cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking);
     B->ev.resize(n + 1);
     for (auto &x : B->ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-    // one graph: every instance's step chain is an independent branch
-    cudaGraph_t g = nullptr;
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaEventRecord(B->ev[n], B->s);
-    for (int k = 0; k < n && e == cudaSuccess; ++k) {
-        tdbem_ctx *c = B->ctx[k];
-        e = cudaStreamWaitEvent(c->s, B->ev[n], 0);
-        if (e == cudaSuccess) e = launch_step_chain(c, c->s);
-        if (e == cudaSuccess) e = cudaEventRecord(B->ev[k], c->s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->s, B->ev[k], 0);
-    }
-    cudaError_t e2 = cudaStreamEndCapture(B->s, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) e = batch_capture(B, 1, &B->graph);
+    if (e == cudaSuccess && B->k > 1) e = batch_capture(B, B->k, &B->graphk);
     if (e != cudaSuccess) {
         tdbem_batch_destroy(B);
         return TDBEM_ERR_CUDA;
     }
     *out = B;
     return TDBEM_OK;
+}
+
+int tdbem_batch_create(tdbem_ctx *const *ctxs, int32_t n, tdbem_batch **out)
+{
+    return tdbem_batch_create_steps(ctxs, n, 1, out);
 }
 
 int tdbem_batch_step(tdbem_batch *B, int32_t nsteps)
@@ -1062,17 +1097,21 @@ int tdbem_batch_step(tdbem_batch *B, int32_t nsteps)
             return TDBEM_ERR_CUDA;
         }
     }
-    for (int n = 0; n < nsteps; ++n) {
-        cudaError_t e = cudaGraphLaunch(B->graph, B->s);
+    // k steps per replay of the long graph, the rest one step per replay
+    for (int n = 0; n < nsteps;) {
+        const bool big = B->graphk && nsteps - n >= B->k;
+        cudaError_t e = cudaGraphLaunch(big ? B->graphk : B->graph, B->s);
         if (e != cudaSuccess) {
             B->err = cudaGetErrorString(e);
             return TDBEM_ERR_CUDA;
         }
+        n += big ? B->k : 1;
     }
     for (tdbem_ctx *c : B->ctx) {
         const int done = std::min(nsteps, c->P.nt - 1 - c->alpha);
         c->alpha += done;
         c->steps_total += done;
+        graph_steps_done(c);
         c->launches[PH_NEAR] += nsteps;
         c->launches[PH_SOLVE] += (int64_t)nsteps * c->solve_iters;
         cudaError_t e = join(B->s, c->user);
@@ -1107,6 +1146,7 @@ void tdbem_batch_destroy(tdbem_batch *B)
     if (!B) return;
     if (B->s) cudaStreamSynchronize(B->s);
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->graphk) cudaGraphExecDestroy(B->graphk);
     for (auto e : B->ev)
         if (e) cudaEventDestroy(e);
     if (B->s) cudaStreamDestroy(B->s);

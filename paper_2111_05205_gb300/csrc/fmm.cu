@@ -133,9 +133,11 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
 
 // M2L operator bank of one level: op[t][blk][row][col] for the offsets
 // o = offs[t] = (dx+3) + 7((dy+3) + 7(dz+3)) (the cell offset S - O) in the
-// order the batched GEMMs use, blk = l-1 (near future l =
-// 1..mu+1) or mu+p (the p-th derivative U^(p) at I_{k+mu+1}, Eq. U_expand),
-// row = a + P3 m, col = b + P3 n:
+// order the batched GEMMs use, blk = l-1 for the near future l = 1..nblk
+// (nblk = mu: the GEMM blocks; blocks past mu would hold l = mu + 1 and the
+// p-th derivative U^(p) at I_{k+mu+1} of Eq. U_expand, which the library
+// forms from their exact low-rank expansion instead), row = a + P3 m,
+// col = b + P3 n:
 //   U(x_a, y_b, t_m, s_n) = (c (t_m - s_n) - r)_+^d / r,
 //   U^(p) = C(d, p) (c (t_m - s_n) - r)_+^(d-p) / r,
 // x_a - y_b = -offset s + ho w_a - hs w_b, t_m - s_n = l T dt + dt + ht (w_m - w_n).
@@ -197,8 +199,9 @@ constexpr int kP2MChunk = 32;
 __global__ void k_p2m(int P3, int P, int Lt, int k, int d, int ns, int smax_hist, const int32_t *__restrict__ cstart,
                       const int32_t *__restrict__ perm, const double *__restrict__ At, const double *__restrict__ As,
                       const double *__restrict__ q, const double *__restrict__ u, const double *__restrict__ wk,
-                      const double *__restrict__ tl, double pref, double *M)
+                      const double *__restrict__ tl, double pref, double *M, StepWhen w)
 {
+    if (w.alpha && (k = when_interval(w)) < 0) return;
     __shared__ double Tq[kP2MChunk][8], Tu[kP2MChunk][8];
     __shared__ int jj[kP2MChunk];
     const int c = blockIdx.x, pt = P / P3;
@@ -275,8 +278,13 @@ __device__ __forceinline__ int find_key_f(const uint64_t *__restrict__ keys, int
 // per axis and T[half][n'][n] = ell_n'((w_n + 2 half - 1)/2) in time.
 __global__ void k_m2m(int ps, int pt, int ncp, const uint64_t *__restrict__ pkey, int ncc,
                       const uint64_t *__restrict__ ckey, const double *__restrict__ Mc, double *Mp,
-                      const double *__restrict__ Sm, const double *__restrict__ Tm, int half)
+                      const double *__restrict__ Sm, const double *__restrict__ Tm, int half, StepWhen w)
 {
+    if (w.alpha) {
+        const int kl = when_interval(w);
+        if (kl < 0) return;
+        half = kl & 1;
+    }
     extern __shared__ double sh[];
     const int P = ps * ps * ps * pt;
     double *b0 = sh, *b1 = sh + P;
@@ -300,13 +308,23 @@ __global__ void k_m2m(int ps, int pt, int ncp, const uint64_t *__restrict__ pkey
     }
 }
 
-// L2L (Section 3): child local += transposed transfer of the parent local.
+// L2L (Section 3): child local += transposed transfer of the parent local,
+// for the child interval kc (slot kc of the child ring) inside the parent
+// interval kc / 2.
 __global__ void k_l2l(int ps, int pt, int ncp, const uint64_t *__restrict__ pkey, int ncc,
-                      const uint64_t *__restrict__ ckey, const double *__restrict__ Lp, double *Lc,
-                      const double *__restrict__ Sm, const double *__restrict__ Tm, int half)
+                      const uint64_t *__restrict__ ckey, const double *__restrict__ Lpr, double *Lcr, int nslot,
+                      const double *__restrict__ Sm, const double *__restrict__ Tm, int kc, StepWhen w)
 {
     extern __shared__ double sh[];
     const int P = ps * ps * ps * pt;
+    if (w.alpha) {
+        const int i = when_interval(w);
+        if (i < 0) return;
+        kc = i + 1;
+    }
+    const int half = kc & 1;
+    const double *Lp = Lpr + (int64_t)((kc / 2) % nslot) * ncp * P;
+    double *Lc = Lcr + (int64_t)(kc % nslot) * ncc * P;
     double *b0 = sh, *b1 = sh + P;
     int c = blockIdx.x;
     int p = find_key_f(pkey, ncp, ckey[c] >> 3);
@@ -330,8 +348,26 @@ __global__ void k_l2l(int ps, int pt, int ncp, const uint64_t *__restrict__ pkey
 //   L_{k+mu+2} <- L_{k+mu+1} + sum_p D_p T^p
 //   A_{p,m} <- A_{p,m} + G_p k^m
 __global__ void k_m2l_recurrence(int64_t n, int d, int mu, int nslot, int k, const double *__restrict__ G, double *D,
-                                 double *Aux, double *ring, const double *__restrict__ cmp, double Tlen)
+                                 double *Aux, double *ring, double Tlen, StepWhen w)
 {
+    if (w.alpha && (k = when_interval(w)) < 0) return;
+    // c_m^p(k) of Eq. cmp, p = 2..d, m = 0..p-2 (index (p-2)(p-1)/2 + m):
+    // C(p, m) ((k-1)^(p-m) - 2 k^(p-m) + (k+1)^(p-m)) (-1)^m, integers
+    // exact in FP64
+    double cmp[kMaxD * (kMaxD - 1) / 2 + 1];
+    for (int p = 2; p <= d; ++p)
+        for (int m = 0; m <= p - 2; ++m) {
+            double binom = 1.0;
+            for (int i = 0; i < m; ++i) binom = binom * (p - i) / (i + 1);
+            const int e = p - m;
+            double a = 1.0, b = 1.0, c = 1.0;
+            for (int i = 0; i < e; ++i) {
+                a *= (double)k - 1.0;
+                b *= (double)k;
+                c *= (double)k + 1.0;
+            }
+            cmp[(p - 2) * (p - 1) / 2 + m] = binom * (a - 2.0 * b + c) * ((m & 1) ? -1.0 : 1.0);
+        }
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         double g[kMaxD + 1];
         for (int p = 1; p <= d; ++p) g[p] = G[(int64_t)(p - 1) * n + e];
@@ -370,9 +406,16 @@ __global__ void k_m2l_recurrence(int64_t n, int d, int mu, int nslot, int k, con
 // element's basis rows and the cell's locals contiguously and the sums are
 // reduced by shuffles.
 __global__ void k_l2p(int ns, int P3, int pt, int Lt, int bie, double c, const int32_t *__restrict__ e2c,
-                      const double *__restrict__ Lloc, const double *__restrict__ Dv, const double *__restrict__ Dn,
-                      const double *__restrict__ tl, const double *__restrict__ dtl, double *far)
+                      const double *__restrict__ ring, int nslot, int nc, int k1, const double *__restrict__ Dv,
+                      const double *__restrict__ Dn, const double *__restrict__ tl, const double *__restrict__ dtl,
+                      double *far, StepWhen w)
 {
+    if (w.alpha) {
+        const int i = when_interval(w);
+        if (i < 0) return;
+        k1 = i + 1;
+    }
+    const double *Lloc = ring + (int64_t)(k1 % nslot) * nc * P3 * pt;
     const int lane = threadIdx.x & 31;
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= ns) return;  // whole warps leave together
@@ -417,8 +460,9 @@ namespace tdbem {
 // stack applies; row a + P3 m + P blk of the product then belongs to node
 // g(a) of O's local (a reduction reads it back through g^-1).
 __global__ void k_m2l_gather(int64_t np, int P3, int P, const int32_t *__restrict__ pS, const uint8_t *__restrict__ pg,
-                             const int16_t *__restrict__ perm, const double *__restrict__ M, double *B)
+                             const int16_t *__restrict__ perm, const double *__restrict__ M, double *B, StepWhen w)
 {
+    if (w.alpha && when_interval(w) < 0) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * P; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t col = e / P;
         const int r = (int)(e % P), b = r % P3;
@@ -441,8 +485,9 @@ __device__ __forceinline__ void split_bf16(double x, int nterm, uint16_t *t)
 // stays zero).
 __global__ void k_m2l_gather_split(int64_t np, int P3, int P, int Kp, int nterm, const int32_t *__restrict__ pS,
                                    const uint8_t *__restrict__ pg, const int16_t *__restrict__ perm,
-                                   const double *__restrict__ M, uint16_t *Bt)
+                                   const double *__restrict__ M, uint16_t *Bt, StepWhen w)
 {
+    if (w.alpha && when_interval(w) < 0) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * P; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t col = e / P;
         const int r = (int)(e % P), b = r % P3;
@@ -505,8 +550,10 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
 template <typename TC>
 __global__ void k_m2l_reduce(int nc, int P3, int P, int nblk, int mu, int nslot, int k, const int64_t *__restrict__ ooff,
                              const int64_t *__restrict__ oidx, const uint8_t *__restrict__ og,
-                             const int16_t *__restrict__ iperm, const TC *__restrict__ C, double *ring, double *G)
+                             const int16_t *__restrict__ iperm, const TC *__restrict__ C, double *ring, double *G,
+                             StepWhen w)
 {
+    if (w.alpha && (k = when_interval(w)) < 0) return;
     __shared__ int64_t cols[kMaxIL];
     __shared__ int32_t gofs[kMaxIL];
     const int R = nblk * P;
@@ -545,17 +592,17 @@ __global__ void k_m2l_reduce(int nc, int P3, int P, int nblk, int mu, int nslot,
 }
 
 // Distance powers between the nodes of a canonical offset's observation and
-// source boxes: kr[c][e][a][b] = r_ab^(e-1) (e = 0: 1/r), e = 0..d-1 (the
+// source boxes: kr[c][e][a][b] = r_ab^(e-1) (e = 0: 1/r), e = 0..d (the
 // slot e = 1, r^0 = 1, is not read), r_ab = |-c s + ho w_a - hs w_b|.
 template <typename T>
 __global__ void k_dist_powers(int ncls, int ps, int d, double s, double hs, double ho, const int32_t *__restrict__ codes,
                               T *out)
 {
     const int P3 = ps * ps * ps;
-    const int64_t n = (int64_t)ncls * d * P3 * P3;
+    const int64_t n = (int64_t)ncls * (d + 1) * P3 * P3;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(e % P3), a = (int)((e / P3) % P3);
-        const int ex = (int)((e / ((int64_t)P3 * P3)) % d), c = (int)(e / ((int64_t)P3 * P3 * d));
+        const int ex = (int)((e / ((int64_t)P3 * P3)) % (d + 1)), c = (int)(e / ((int64_t)P3 * P3 * (d + 1)));
         const int o = codes[c];
         const int dx = o % 7 - 3, dy = (o / 7) % 7 - 3, dz = o / 49 - 3;
         const int a1 = a % ps, a2 = (a / ps) % ps, a3 = a / (ps * ps);
@@ -638,29 +685,35 @@ __device__ __forceinline__ T gen_from(double v)
     }
 }
 
-// The derivative contributions G_p (p = 1..d) of one level's M2L (the
-// U^(p) of Eq. U_expand at I_{k+mu+1}, applied to the moments of every
-// interaction pair of a cell), from the binomial expansion of
+// The last near-future block (p = 0: the local L_{k+mu+1,k} itself) and the
+// derivative contributions G_p (p = 1..d) of one level's M2L (the U^(p) of
+// Eq. U_expand at I_{k+mu+1}, applied to the moments of every interaction
+// pair of a cell), from the binomial expansion of
 // U^(p) = C(d,p) z^q / r, q = d - p, z = A + c ht w_m - c ht w_n - r,
-// A = c ((mu+1) T + 1) dt:
+// A = c ((mu+1) T + 1) dt (mu is chosen so that z > 0 on the whole node
+// domain of I_{k+mu+1} x J_k, so the kernel there is this polynomial):
 //   G_p[a, m] = C(d,p) sum_{i+j+k=q} q!/(i! j! k!) (c ht w_m)^i (-c ht)^j
 //               sum_{e<=k} C(k,e) A^(k-e) (-1)^e F_{e,j}[a],
 //   F_{e,j}[a] = sum_pairs sum_b r_ab^(e-1) mu_j[b],  mu_j[b] = sum_n w_n^j M[b, n]
 // (the pair's moment, node indices permuted by its symmetry element).  So
-// the derivative rows need spatial products only (e + j <= d - 1; e = 1 is
-// a plain sum) instead of d P x P operator blocks per pair; they are summed
-// in FP64 (FP64 form) or double-float (tensor-core forms), since the
-// distant-future recurrence amplifies their rounding with the square of the
-// number of intervals.  One CTA per observation cell; per pair, one warp
+// these rows need spatial products only (e + j <= d; e = 1 is a plain sum)
+// instead of d + 1 P x P operator blocks per pair; they are summed in FP64
+// (FP64 form) or double-float (tensor-core forms): the distant-future
+// recurrence starts from L_{k+mu+1} and adds the G_p of every later
+// interval, so it carries their rounding into every later interval (an
+// FP32-grade L_{k+mu+1} made the march drift linearly in time), and
+// amplifies the G_p's with the square of the number of intervals.  One CTA per observation cell; per pair, one warp
 // per observation node at a time, its lanes striding the source nodes.
-// Kernel 1: time moments of every GEMM column (pair), node indices
-// permuted by the column's symmetry element:
+// Kernel 1: time moments j = 0..d of every GEMM column (pair), node indices
+// permuted by the column's symmetry element (template D = d + 1 moments):
 //   mu[col][j][b] = sum_n w_n^j M_S[g(b) + P3 n],  ssum[col][j] = sum_b mu[col][j][b].
 template <typename T, int D>
 __global__ void k_deriv_moments(int64_t np, int P3, int pt, const int32_t *__restrict__ pS,
                                 const uint8_t *__restrict__ pg, const int16_t *__restrict__ perm,
-                                const double *__restrict__ wt, const double *__restrict__ M, T *mu, double *ssum)
+                                const double *__restrict__ wt, const double *__restrict__ M, T *mu, double *ssum,
+                                StepWhen w)
 {
+    if (w.alpha && when_interval(w) < 0) return;
     const int64_t col = blockIdx.x;
     const int P = P3 * pt;
     const int Sc = pS[col], g = pg[col];
@@ -710,18 +763,20 @@ __global__ void k_deriv_moments(int64_t np, int P3, int pt, const int32_t *__res
 // Kernel 2: per symmetry class, the distance-power matrices times the
 // columns' time moments, in FP64 or double-float on the CUDA cores:
 //   Fp[col][e][j][a] = sum_b r_ab^(e-1) mu[col][j][b]  (e != 1, e + j <= D - 1),
-// a in the canonical node order.  One CTA per (class, 8 columns), one
-// thread per row a; the matrices go through shared memory 32 columns at a
-// time (rows padded to 33 entries), so each chunk serves 8 columns.
+// a in the canonical node order (D = d + 1).  One CTA per (class, 8
+// columns), one thread per row a; the matrices go through shared memory cw
+// (32, or 16 for the largest boxes) columns at a time (rows padded to cw + 1
+// entries), so each chunk serves 8 columns.
 constexpr int kDerivCols = 8;
 
 template <typename T, int D>
-__global__ void k_deriv_products(int P3, const int4 *__restrict__ jobs, const T *__restrict__ kr,
-                                 const T *__restrict__ mu, T *Fp)
+__global__ void __launch_bounds__(512) k_deriv_products(int P3, int cw, const int4 *__restrict__ jobs, const T *__restrict__ kr,
+                                 const T *__restrict__ mu, T *Fp, StepWhen w)
 {
+    if (w.alpha && when_interval(w) < 0) return;
     extern __shared__ double shm_d[];
     T *mus = reinterpret_cast<T *>(shm_d);    // [kDerivCols][D][P3]
-    T *kc = mus + kDerivCols * D * P3;        // [P3][33]
+    T *kc = mus + kDerivCols * D * P3;        // [P3][cw + 1]
     const int4 job = jobs[blockIdx.x];        // class, first column, columns
     const int cls = job.x, ncol = job.z;
     const int64_t col0 = job.y;
@@ -739,17 +794,17 @@ __global__ void k_deriv_products(int P3, const int4 *__restrict__ jobs, const T 
 #pragma unroll
             for (int j = 0; j < D; ++j) acc[t][j] = gen_from<T>(0.0);
         const T *K = kr + ((int64_t)cls * D + e) * P3 * P3;
-        for (int b0 = 0; b0 < P3; b0 += 32) {
+        for (int b0 = 0; b0 < P3; b0 += cw) {
             __syncthreads();
-            for (int x = threadIdx.x; x < P3 * 32; x += blockDim.x) {
-                const int row = x >> 5, cc = x & 31;
-                kc[row * 33 + cc] = (b0 + cc < P3) ? K[(int64_t)row * P3 + b0 + cc] : gen_from<T>(0.0);
+            for (int x = threadIdx.x; x < P3 * cw; x += blockDim.x) {
+                const int row = x / cw, cc = x % cw;
+                kc[row * (cw + 1) + cc] = (b0 + cc < P3) ? K[(int64_t)row * P3 + b0 + cc] : gen_from<T>(0.0);
             }
             __syncthreads();
             if (r < P3) {
-                const int nb = min(32, P3 - b0);
+                const int nb = min(cw, P3 - b0);
                 for (int cc = 0; cc < nb; ++cc) {
-                    const T x = kc[r * 33 + cc];
+                    const T x = kc[r * (cw + 1) + cc];
 #pragma unroll
                     for (int t = 0; t < kDerivCols; ++t)
 #pragma unroll
@@ -769,15 +824,18 @@ __global__ void k_deriv_products(int P3, const int4 *__restrict__ jobs, const T 
 
 // Kernel 3: per observation cell, F_{e,j}[a'] = sum over its pairs (list
 // order) of Fp[col][e][j][g^-1(a')], and S_j = sum of ssum; then
-// G_p[a', m] = sum_{e,j} coef[p-1][m][e][j] F_{e,j}[a'] (F_{1,j} = S_j), with
+// V_p[a', m] = sum_{e,j} coef[p][m][e][j] F_{e,j}[a'] (F_{1,j} = S_j), with
 // the binomial-expansion coefficients of Eq. U_expand tabulated per level
-// at setup (deriv_coef_table).
+// at setup (deriv_coef_table): V_0 is added to the local L_{k+mu+1} (ring
+// slot k + mu + 1), V_p (p >= 1) is G_p.  D = d + 1.
 template <typename T, int D>
-__global__ void k_deriv_assemble(int nc, int P3, int pt, const int64_t *__restrict__ ooff,
+__global__ void k_deriv_assemble(int nc, int P3, int pt, int nslot, int k, int mu, const int64_t *__restrict__ ooff,
                                  const int64_t *__restrict__ oidx, const uint8_t *__restrict__ og,
                                  const int16_t *__restrict__ iperm, const T *__restrict__ Fp,
-                                 const double *__restrict__ ssum, const double *__restrict__ coef, double *G)
+                                 const double *__restrict__ ssum, const double *__restrict__ coef, double *ring,
+                                 double *G, StepWhen w)
 {
+    if (w.alpha && (k = when_interval(w)) < 0) return;
     const int O = blockIdx.x;
     const int P = P3 * pt;
     const int64_t t0 = ooff[O], t1 = ooff[O + 1];
@@ -817,36 +875,69 @@ __global__ void k_deriv_assemble(int nc, int P3, int pt, const int64_t *__restri
                 for (int e = 0; e < D; ++e)
 #pragma unroll
                     for (int j = 0; j + e < D; ++j) v += cf[e * D + j] * Fv[e][j];
-                G[((int64_t)p * nc + O) * P + r + (int64_t)P3 * m] = v;
+                if (p == 0)
+                    ring[((int64_t)((k + mu + 1) % nslot) * nc + O) * P + r + (int64_t)P3 * m] += v;
+                else
+                    G[((int64_t)(p - 1) * nc + O) * P + r + (int64_t)P3 * m] = v;
             }
     }
 }
 
-template <typename T, int D>
-static cudaError_t launch_deriv_d(int nc, int P3, int pt, const FmmLevel &V, const double *wt,
-                                  const int16_t *perm, const int16_t *iperm, cudaStream_t s)
+// Shared memory of the products kernel and its chunk width (32 columns of
+// the distance-power matrices, 16 where 32 do not fit).
+static size_t deriv_shm(int D, int P3, size_t el, int *cw)
 {
-    T *mu = reinterpret_cast<T *>(V.dmu), *Fp = reinterpret_cast<T *>(V.dF);
+    *cw = 32;
+    size_t b = ((size_t)kDerivCols * D * P3 + (size_t)P3 * 33) * el;
+    if (b > (size_t)kTcSmemBudget) {
+        *cw = 16;
+        b = ((size_t)kDerivCols * D * P3 + (size_t)P3 * 17) * el;
+    }
+    return b;
+}
+
+// D = d + 1 (moments j = 0..d, distance powers e = 0..d, rows p = 0..d).
+template <typename T, int D>
+static cudaError_t launch_deriv_d(int nc, int P3, int pt, int nslot, int k, int mu, const FmmLevel &V,
+                                  const double *wt, const int16_t *perm, const int16_t *iperm, cudaStream_t s,
+                                  StepWhen w)
+{
+    T *dm = reinterpret_cast<T *>(V.dmu), *Fp = reinterpret_cast<T *>(V.dF);
     const int bdim = std::max(128, (P3 + 31) / 32 * 32);
-    k_deriv_moments<T, D><<<(unsigned)V.np, 128, 0, s>>>(V.np, P3, pt, V.pS, V.pg, perm, wt, V.M, mu, V.dss);
-    const size_t shm = ((size_t)kDerivCols * D * P3 + (size_t)P3 * 33) * sizeof(T);
-    if (shm > 48 * 1024)
-        cudaFuncSetAttribute(k_deriv_products<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_deriv_products<T, D><<<V.njobs, bdim, shm, s>>>(P3, V.djobs, reinterpret_cast<const T *>(V.kr), mu, Fp);
-    k_deriv_assemble<T, D><<<nc, 256, 0, s>>>(nc, P3, pt, V.ooff, V.oidx, V.og, iperm, Fp, V.dss, V.dcoef, V.G);
+    k_deriv_moments<T, D><<<(unsigned)V.np, 128, 0, s>>>(V.np, P3, pt, V.pS, V.pg, perm, wt, V.M, dm, V.dss, w);
+    int cw = 32;
+    const size_t shm = deriv_shm(D, P3, sizeof(T), &cw);
+    if (shm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_deriv_products<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)shm);
+        if (e != cudaSuccess) return e;
+    }
+    k_deriv_products<T, D><<<V.njobs, bdim, shm, s>>>(P3, cw, V.djobs, reinterpret_cast<const T *>(V.kr), dm, Fp, w);
+    k_deriv_assemble<T, D><<<nc, 256, 0, s>>>(nc, P3, pt, nslot, k, mu, V.ooff, V.oidx, V.og, iperm, Fp, V.dss,
+                                              V.dcoef, V.ring, V.G, w);
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_deriv(int d, int nc, int P3, int pt, const FmmLevel &V, const double *wt,
-                                const int16_t *perm, const int16_t *iperm, cudaStream_t s)
+static cudaError_t launch_deriv(int d, int nc, int P3, int pt, int nslot, int k, int mu, const FmmLevel &V,
+                                const double *wt, const int16_t *perm, const int16_t *iperm, cudaStream_t s,
+                                StepWhen w)
 {
     switch (d) {
-    case 1: return launch_deriv_d<T, 1>(nc, P3, pt, V, wt, perm, iperm, s);
-    case 2: return launch_deriv_d<T, 2>(nc, P3, pt, V, wt, perm, iperm, s);
-    case 3: return launch_deriv_d<T, 3>(nc, P3, pt, V, wt, perm, iperm, s);
-    default: return launch_deriv_d<T, 4>(nc, P3, pt, V, wt, perm, iperm, s);
+    case 1: return launch_deriv_d<T, 2>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
+    case 2: return launch_deriv_d<T, 3>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
+    case 3: return launch_deriv_d<T, 4>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
+    default: return launch_deriv_d<T, 5>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
     }
+}
+
+// Zeroes a level's moment accumulator after its M2M (graph-replayed steps;
+// plain stepping uses a memset).
+__global__ void k_zero_when(int64_t n, double *x, StepWhen w)
+{
+    if (when_interval(w) < 0) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] = 0.0;
 }
 
 
@@ -906,19 +997,6 @@ cudaError_t falloc(tdbem_ctx *c, T **p, size_t n)
         e = cudaMemsetAsync(q, 0, std::max<size_t>(n * sizeof(T), 16), c->s);
     }
     return e;
-}
-
-// c_m^p(k) of Eq. cmp for p = 2..d, m = 0..p-2 (index (p-2)(p-1)/2 + m).
-void cmp_table(int d, int k, double *out)
-{
-    for (int p = 2; p <= d; ++p)
-        for (int m = 0; m <= p - 2; ++m) {
-            double binom = 1.0;
-            for (int i = 0; i < m; ++i) binom = binom * (p - i) / (i + 1);
-            int e = p - m;
-            double v = pow((double)k - 1.0, e) - 2.0 * pow((double)k, e) + pow((double)k + 1.0, e);
-            out[(p - 2) * (p - 1) / 2 + m] = binom * v * ((m & 1) ? -1.0 : 1.0);
-        }
 }
 
 }  // namespace
@@ -992,7 +1070,7 @@ static std::vector<TcTile> m2l_tiles(const Fmm &F, const FmmLevel &V, int bn, co
     return t;
 }
 
-static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V)
+static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V, StepWhen w = StepWhen{})
 {
     const Fmm &F = c->fmm;
     TcGemmArgs g{};
@@ -1009,15 +1087,17 @@ static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V)
     g.C = V.C32;
     g.tiles = V.tiles;
     g.err = c->d_flag;
+    g.when = w;
     return g;
 }
 
 // The products of one M2L application: every class's canonical operator
 // stack times its gathered columns.
-static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V)
+static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V, StepWhen w = StepWhen{})
 {
     Fmm &F = c->fmm;
-    if (c->split) return tc_gemm_launch(V.mapA, V.mapB, m2l_args(c, V), V.ntiles, V.tile_n, c->s);
+    if (c->split) return tc_gemm_launch(V.mapA, V.mapB, m2l_args(c, V, w), V.ntiles, V.tile_n, c->s);
+    if (w.alpha) return cudaErrorNotSupported;  // the FP64 form's library GEMMs cannot be predicated
     const double one = 1.0, zero = 0.0;
     for (int ci = 0; ci < V.ncls; ++ci) {
         const int64_t c0 = V.cbase[ci], n = V.cbase[ci + 1] - c0;
@@ -1033,12 +1113,14 @@ static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V)
     return cudaSuccess;
 }
 
-// Coefficients of the derivative rows (Eq. U_expand expanded binomially in
-// the time nodes): U^(p) = C(d,p) z^q / r, q = d - p, z = A + cht w_m - cht w_n
-// - r, A = c ((mu+1) T + 1) dt, cht = c T dt / 2, gives
-// G_p[a,m] = sum_{e,j} coef[p-1][m][e][j] F_{e,j}[a] with F_{e,j}[a] =
+// Coefficients of the rows of the last near-future block (p = 0) and the
+// derivative rows (p = 1..d) (Eq. U_expand expanded binomially in the time
+// nodes): U^(p) = C(d,p) z^q / r, q = d - p, z = A + cht w_m - cht w_n - r,
+// A = c ((mu+1) T + 1) dt, cht = c T dt / 2, gives
+// V_p[a,m] = sum_{e,j} coef[p][m][e][j] F_{e,j}[a] with F_{e,j}[a] =
 // sum_b r_ab^(e-1) sum_n w_n^j M[b,n] and
-// coef = C(d,p) sum_{i+j+k=q, k>=e} C(q,i) C(q-i,j) (cht w_m)^i (-cht)^j C(k,e) A^(k-e) (-1)^e.
+// coef = C(d,p) sum_{i+j+k=q, k>=e} C(q,i) C(q-i,j) (cht w_m)^i (-cht)^j C(k,e) A^(k-e) (-1)^e
+// (layout [d+1][pt][d+1][d+1]).
 static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht)
 {
     auto binom = [](int n, int k) {
@@ -1046,8 +1128,9 @@ static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht)
         for (int i = 0; i < k; ++i) v = v * (n - i) / (i + 1);
         return v;
     };
-    std::vector<double> t((size_t)d * pt * d * d, 0.0);
-    for (int p = 1; p <= d; ++p) {
+    const int E = d + 1;
+    std::vector<double> t((size_t)E * pt * E * E, 0.0);
+    for (int p = 0; p <= d; ++p) {
         const int q = d - p;
         for (int m = 0; m < pt; ++m) {
             const double wm = h_cheb(pt, m);
@@ -1055,7 +1138,7 @@ static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht)
                 for (int j = 0; i + j <= q; ++j) {
                     const int k = q - i - j;
                     for (int e = 0; e <= k; ++e)
-                        t[(((size_t)(p - 1) * pt + m) * d + e) * d + j] +=
+                        t[(((size_t)p * pt + m) * E + e) * E + j] +=
                             binom(d, p) * binom(q, i) * binom(q - i, j) * std::pow(cht * wm, i) * std::pow(-cht, j) *
                             binom(k, e) * std::pow(A, k - e) * ((e & 1) ? -1.0 : 1.0);
                 }
@@ -1139,6 +1222,13 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         why = "FMM needs ps^3 pt <= 4096";
         return cudaSuccess;
     }
+    {
+        int cw = 0;
+        if (deriv_shm(d + 1, F.P3, c->split ? sizeof(float2) : sizeof(double), &cw) > (size_t)kTcSmemBudget) {
+            why = "FMM: ps^3 too large for the exact rows at this B-spline order";
+            return cudaSuccess;
+        }
+    }
     double box[4];
     F_TRY(cudaMemcpy(box, c->tree.box, sizeof(box), cudaMemcpyDeviceToHost));
     unsigned long long *d_rho = nullptr;
@@ -1174,7 +1264,16 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     F.nd = d * (d - 1) / 2;
     F.nslot = F.mu + 2;
     const int P = F.P, P3 = F.P3, ps = F.ps, pt = F.pt;
-    F.ngb = F.mu + 1;  // operator blocks applied as GEMMs: the near future
+    if (2 * P * sizeof(double) > 48 * 1024) {
+        // M2M and L2L stage two [P] tensors in shared memory (64 KB at P = 4096)
+        F_TRY(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * P * sizeof(double))));
+        F_TRY(cudaFuncSetAttribute(k_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * P * sizeof(double))));
+    }
+    // operator blocks applied as GEMMs: the near future l = 1..mu; the block
+    // l = mu + 1 lies wholly in the polynomial regime and is formed exactly
+    // with the derivative rows (k_deriv_*), since the recurrence of Formula 1
+    // starts from it
+    F.ngb = F.mu;
     F.R = F.ngb * P;
     F.Rp = (F.R + kTcBM - 1) / kTcBM * kTcBM;
     F.Kp = (P + kTcBK - 1) / kTcBK * kTcBK;
@@ -1267,7 +1366,6 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         F_TRY(cudaMemcpyAsync(F.wt, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
     }
     F_TRY(cudaMemcpyAsync(F.Tm, tm.data(), tm.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
-    F_TRY(falloc(c, &F.cmp, 16));
     F_TRY(falloc(c, &F.far, (size_t)F.Lt * ns));
 
     for (int l = 2; l <= L; ++l) {
@@ -1379,7 +1477,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                                                         c->P.c, V.ncls, d_codes, op);
             F_TRY(cudaGetLastError());
             // distance powers of the derivative rows (Eq. U_expand)
-            const size_t nkr = (size_t)V.ncls * d * P3 * P3;
+            const size_t nkr = (size_t)V.ncls * (d + 1) * P3 * P3;
             if (c->split) {
                 float2 *kr = nullptr;
                 F_TRY(falloc(c, &kr, nkr));
@@ -1392,13 +1490,14 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                 V.kr = kr;
             }
             F_TRY(cudaGetLastError());
-            V.flops_deriv = 2.0 * P3 * P3 * (double)V.np * (d * (d + 1) / 2 - (d >= 2 ? d - 1 : 0));
+            // spatial products per pair: (e, j) with e + j <= d, e != 1
+            V.flops_deriv = 2.0 * P3 * P3 * (double)V.np * ((d + 1) + (d - 1) * d / 2);
             {
                 // work of the derivative rows: buffers and (class, 8-column) jobs
                 const size_t el = c->split ? sizeof(float2) : sizeof(double);
-                F_TRY(falloc(c, (char **)&V.dmu, (size_t)V.np * d * P3 * el));
-                F_TRY(falloc(c, (char **)&V.dF, (size_t)V.np * d * d * P3 * el));
-                F_TRY(falloc(c, &V.dss, (size_t)V.np * d));
+                F_TRY(falloc(c, (char **)&V.dmu, (size_t)V.np * (d + 1) * P3 * el));
+                F_TRY(falloc(c, (char **)&V.dF, (size_t)V.np * (d + 1) * (d + 1) * P3 * el));
+                F_TRY(falloc(c, &V.dss, (size_t)V.np * (d + 1)));
                 std::vector<int4> jobs;
                 for (int ci = 0; ci < V.ncls; ++ci)
                     for (int64_t c0 = V.cbase[ci]; c0 < V.cbase[ci + 1]; c0 += kDerivCols)
@@ -1446,101 +1545,124 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
 // Far field at the boundary after leaf interval k (every source of J_k is
 // known): P2M, M2M + M2L up the levels whose interval ended, L2L down the
 // levels whose interval starts, and L2P of the leaf local of I_{k+1}.
-cudaError_t fmm_boundary(tdbem_ctx *c, int k)
+//
+// graph = true (capture of a graph-replayed step): every pass of every level
+// is launched, each kernel reading the step from c->d_alpha and deciding on
+// the device whether it runs (StepWhen); k is not used.  The phase timers
+// and counters of plain stepping are left alone.
+cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
 {
     Fmm &F = c->fmm;
     const int L = F.L, d = c->P.d, P = F.P;
     cudaStream_t s = c->s;
     const double pref = 1.0 / (4.0 * M_PI * pow(c->cdt, d));
     const TreeLevel &TL = c->tree.levels[L];
-    ++c->far_kernels;
+    auto when = [&](int span) {
+        StepWhen w;
+        if (graph) {
+            w.alpha = c->d_alpha;
+            w.alim = c->P.nt - 1;
+            w.lt = F.Lt;
+            w.span = span;
+        }
+        return w;
+    };
+    if (!graph) ++c->far_kernels;
     k_p2m<<<TL.nc, 128, 0, s>>>(F.P3, P, F.Lt, k, d, c->ns, c->P.nt - 2, TL.cstart, c->tree.perm, F.At, F.As, c->d_q,
-                                c->d_u, F.wk, F.tl, pref, F.lev[L].M);
+                                c->d_u, F.wk, F.tl, pref, F.lev[L].M, when(1));
     F_TRY(cudaGetLastError());
     size_t shm = 2 * P * sizeof(double);
     for (int l = L; l >= 2; --l) {
         int span = 1 << (L - l);
-        if ((k + 1) % span) break;
-        int kl = (k + 1) / span - 1;
+        if (!graph && (k + 1) % span) break;
+        int kl = graph ? 0 : (k + 1) / span - 1;
+        const StepWhen w = when(span);
         FmmLevel &V = F.lev[l];
         const TreeLevel &T = c->tree.levels[l];
         // M2L for source interval kl of this level: gather (permuted by each
         // column's symmetry), one GEMM per symmetry class, per-cell
         // reduction into the locals (near future) and G
         if (V.np > 0) {
-            cudaEvent_t ev;
-            phase_begin(c, &ev);
+            cudaEvent_t ev = nullptr;
+            if (!graph) phase_begin(c, &ev);
             const int64_t n = V.np * P;
             const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-            c->far_kernels += 3;  // gather, products, reduction
+            if (!graph) c->far_kernels += 3;  // gather, products, reduction
             if (c->split)
-                k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt);
+                k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt, w);
             else
-                k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf);
+                k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf, w);
             F_TRY(cudaGetLastError());
-            {
+            if (graph) {
+                F_TRY(m2l_products(c, V, w));
+            } else {
                 cudaEvent_t eg;
                 phase_begin(c, &eg);
-                F_TRY(m2l_products(c, V));
+                F_TRY(m2l_products(c, V, w));
                 phase_end(c, PH_GEMM, eg);
                 c->launches[PH_GEMM] += c->split ? 1 : V.ncls;
                 c->gemm_tc_flops += V.flops_app * (c->split ? F.nprod : 1);
             }
             if (c->split)
                 k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx, V.og,
-                                                         F.iperm, V.C32, V.ring, V.G);
+                                                         F.iperm, V.C32, V.ring, V.G, w);
             else
                 k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx,
-                                                          V.og, F.iperm, V.Cbuf, V.ring, V.G);
+                                                          V.og, F.iperm, V.Cbuf, V.ring, V.G, w);
             F_TRY(cudaGetLastError());
-            // derivative contributions G (exact low-rank form of Eq. U_expand)
-            c->far_kernels += 3;
+            // the block L_{k+mu+1,k} and the derivative contributions G (exact
+            // low-rank form of Eq. U_expand)
             if (c->split)
-                F_TRY(launch_deriv<float2>(d, V.nc, F.P3, F.pt, V, F.wt, F.perm, F.iperm, s));
+                F_TRY(launch_deriv<float2>(d, V.nc, F.P3, F.pt, F.nslot, kl, F.mu, V, F.wt, F.perm, F.iperm, s, w));
             else
-                F_TRY(launch_deriv<double>(d, V.nc, F.P3, F.pt, V, F.wt, F.perm, F.iperm, s));
-            phase_end(c, PH_M2L, ev);
-            c->launches[PH_M2L] += 1;
-            c->m2l_flops += V.flops_app + V.flops_deriv;
-        } else {
+                F_TRY(launch_deriv<double>(d, V.nc, F.P3, F.pt, F.nslot, kl, F.mu, V, F.wt, F.perm, F.iperm, s, w));
+            if (!graph) {
+                c->far_kernels += 3;
+                phase_end(c, PH_M2L, ev);
+                c->launches[PH_M2L] += 1;
+                c->m2l_flops += V.flops_app + V.flops_deriv;
+            }
+        } else if (!graph) {
+            // (G of a level without pairs stays zero from its allocation on)
             F_TRY(cudaMemsetAsync(V.G, 0, (size_t)d * V.nc * P * sizeof(double), s));
         }
-        double cm[16] = {0};
-        cmp_table(d, kl, cm);
-        F_TRY(cudaMemcpyAsync(F.cmp, cm, sizeof(cm), cudaMemcpyHostToDevice, s));
         int64_t n = (int64_t)V.nc * P;
-        ++c->far_kernels;
+        if (!graph) ++c->far_kernels;
         k_m2l_recurrence<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
-            n, d, F.mu, F.nslot, kl, V.G, V.D, V.A, V.ring, F.cmp, V.Tlen);
+            n, d, F.mu, F.nslot, kl, V.G, V.D, V.A, V.ring, V.Tlen, w);
         F_TRY(cudaGetLastError());
         // M2M into the parent, then clear this level's accumulator
         if (l > 2) {
             FmmLevel &Pv = F.lev[l - 1];
             const TreeLevel &PT = c->tree.levels[l - 1];
-            ++c->far_kernels;
-            k_m2m<<<Pv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, PT.ckey, V.nc, T.ckey, V.M, Pv.M, V.Sm, F.Tm, kl & 1);
+            if (!graph) ++c->far_kernels;
+            k_m2m<<<Pv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, PT.ckey, V.nc, T.ckey, V.M, Pv.M, V.Sm, F.Tm, kl & 1, w);
             F_TRY(cudaGetLastError());
         }
-        F_TRY(cudaMemsetAsync(V.M, 0, (size_t)V.nc * P * sizeof(double), s));
+        if (graph) {
+            k_zero_when<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(n, V.M, w);
+            F_TRY(cudaGetLastError());
+        } else {
+            F_TRY(cudaMemsetAsync(V.M, 0, (size_t)V.nc * P * sizeof(double), s));
+        }
     }
     // L2L into the levels whose interval starts at leaf interval k + 1
     for (int l = 2; l < L; ++l) {
         int span = 1 << (L - l - 1);  // leaf intervals per level-(l+1) interval
-        if ((k + 1) % span) continue;
-        int kc = (k + 1) / span, kp = kc / 2;
+        if (!graph && (k + 1) % span) continue;
+        int kc = graph ? 0 : (k + 1) / span;
         FmmLevel &Pv = F.lev[l], &Cv = F.lev[l + 1];
-        ++c->far_kernels;
+        if (!graph) ++c->far_kernels;
         k_l2l<<<Cv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, c->tree.levels[l].ckey, Cv.nc, c->tree.levels[l + 1].ckey,
-                                      Pv.ring + (size_t)(kp % F.nslot) * Pv.nc * P,
-                                      Cv.ring + (size_t)(kc % F.nslot) * Cv.nc * P, Cv.So, F.Tm, kc & 1);
+                                      Pv.ring, Cv.ring, F.nslot, Cv.So, F.Tm, kc, when(span));
         F_TRY(cudaGetLastError());
     }
     // L2P for observation interval k + 1
     FmmLevel &V = F.lev[L];
-    ++c->far_kernels;
-    k_l2p<<<(int)(((int64_t)c->ns * 32 + 127) / 128), 128, 0, s>>>(c->ns, F.P3, F.pt, F.Lt, c->P.bie, c->P.c, c->tree.e2c,
-                                              V.ring + (size_t)((k + 1) % F.nslot) * V.nc * P, F.Dv, F.Dn, F.tl,
-                                              F.dtl, F.far);
+    if (!graph) ++c->far_kernels;
+    k_l2p<<<(int)(((int64_t)c->ns * 32 + 127) / 128), 128, 0, s>>>(c->ns, F.P3, F.pt, F.Lt, c->P.bie, c->P.c,
+                                                                    c->tree.e2c, V.ring, F.nslot, V.nc, k + 1, F.Dv,
+                                                                    F.Dn, F.tl, F.dtl, F.far, when(1));
     return cudaGetLastError();
 }
 

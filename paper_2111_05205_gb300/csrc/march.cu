@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
                                                               const double *__restrict__ exc, Incident inc,
                                                               const double *__restrict__ xc,
                                                               const double *__restrict__ nrm,
-                                                              const double *__restrict__ far, int alim, double *b)
+                                                              const double *__restrict__ far, int far_lt, int alim,
+                                                              double *b)
 {
     __shared__ double red[kNearWarps];
     if (alpha_dev) {
@@ -355,7 +356,9 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
             e = exc[i];
         else if (inc.on)
             e = incident_term(inc, xc + 3 * i, nrm + 3 * i, alpha);
-        if (far) e += far[i];
+        // far field of the step: far[(alpha - 1) % Lt] when the kernel reads
+        // the step from the device (far_lt = Lt), else already offset
+        if (far) e += far[(far_lt ? (int64_t)((alpha - 1) % far_lt) * ns : 0) + i];
         b[i] = t - e;
     }
 }
@@ -372,7 +375,7 @@ static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, c
     const int32_t *hcol = (SPLIT && c->d_hcol) ? c->d_hcol : c->d_col;
     k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, hcol, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
-                                       c->d_n, d_far, c->P.nt - 1, c->d_b);
+                                       c->d_n, d_far, c->alpha_dev_on && d_far ? c->fmm.Lt : 0, c->P.nt - 1, c->d_b);
     return cudaGetLastError();
 }
 
@@ -484,41 +487,6 @@ __global__ void k_jacobi(int ns, int width, const double *__restrict__ aoff, con
         jacobi_store(i, x, row, phi, u, q, us, qs, hpos, flag);
     else
         xout[i] = x;
-}
-
-// Grid-wide barrier of a cooperative launch (every CTA resident): arrival
-// counter bar[0], generation bar[1].  The wait is bounded: after
-// kBarrierPolls polls the CTA records a timeout (flag bit 4) and goes on,
-// so a barrier that cannot complete ends the kernel with an error that the
-// host reports, never with a hang.
-constexpr unsigned kBarrierPolls = 1u << 22;  // with 64 ns sleeps: about 0.3 s
-
-__device__ __forceinline__ void grid_barrier(unsigned *bar, int *flag)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            // poll with short sleeps (polling without them measured slower:
-            // every waiting CTA then hammers the same word)
-            unsigned polls = 0;
-            while (*gen == g) {
-                if (++polls > kBarrierPolls) {
-                    atomicOr(flag, 4);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
 }
 
 // All K sweeps of one step in one cooperative launch (rows grid-strided),

@@ -130,17 +130,12 @@ __device__ void sai_forward(int W, int H, const __half *w1, const __half *b1, co
     }
 }
 
-// One training pass over the rows of one matrix: loss of every row and the
-// gradients of the weights (FP32, accumulated with atomics).  Residual of
-// row i: r_l = sum_k M_{i,j_k} A_{j_k, l} - delta_il over the columns l of
-// the rows j_k.
-__global__ void k_sai_train_rows(int ns, int ell_w, int W, int H, const double *__restrict__ aoff,
-                                 const int32_t *__restrict__ acol, const double *__restrict__ ainv,
-                                 const double *__restrict__ xc, double cdt, const __half *__restrict__ w16,
-                                 float *grad, float *loss)
+// Loss and gradient contributions of row i, added to grad[] and *loss.
+__device__ void sai_row_grad(int i, int ns, int ell_w, int W, int H, const double *__restrict__ aoff,
+                             const int32_t *__restrict__ acol, const double *__restrict__ ainv,
+                             const double *__restrict__ xc, double cdt, const __half *__restrict__ w16, float *grad,
+                             float *loss)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
     const int F = kSaiF * W;
     const __half *w1 = w16, *b1 = w1 + H * F, *w2 = b1 + H, *b2 = w2 + W * H;
     float *g1 = grad, *gb1 = g1 + H * F, *g2 = gb1 + H, *gb2 = g2 + W * H;
@@ -200,6 +195,28 @@ __global__ void k_sai_train_rows(int ns, int ell_w, int W, int H, const double *
     }
 }
 
+// One training pass over the rows of one matrix: loss of every row and the
+// gradients of the weights (FP32).  Residual of row i: r_l = sum_k
+// M_{i,j_k} A_{j_k, l} - delta_il over the columns l of the rows j_k.  The
+// CTA's rows add their gradients in shared memory (nw floats), then the CTA
+// adds its sums to the global gradient, one atomic per non-zero weight.
+__global__ void k_sai_train_rows(int ns, int ell_w, int W, int H, int nw, const double *__restrict__ aoff,
+                                 const int32_t *__restrict__ acol, const double *__restrict__ ainv,
+                                 const double *__restrict__ xc, double cdt, const __half *__restrict__ w16,
+                                 float *grad, float *loss)
+{
+    extern __shared__ float gsh[];  // [nw] gradient, [1] loss
+    for (int e = threadIdx.x; e <= nw; e += blockDim.x) gsh[e] = 0.f;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ns) sai_row_grad(i, ns, ell_w, W, H, aoff, acol, ainv, xc, cdt, w16, gsh, gsh + nw);
+    __syncthreads();
+    for (int e = threadIdx.x; e <= nw; e += blockDim.x) {
+        const float v = gsh[e];
+        if (v != 0.f) atomicAdd(e < nw ? grad + e : loss, v);
+    }
+}
+
 // Adam on the FP32 master weights; FP16 copies for the forward pass.
 __global__ void k_sai_adam(int n, float *w, float *m, float *v, const float *grad, float scale, float lr, float b1,
                            float b2, float eps, int t, __half *w16)
@@ -234,10 +251,49 @@ __global__ void k_sai_apply_net(int ns, int ell_w, int W, int H, const double *_
     }
 }
 
-// One preconditioned sweep x' = x + M (b - A x) (x == nullptr: x' = M b),
-// the residual of each row j of M's pattern recomputed on the fly (one
-// launch per sweep, as the Jacobi sweep).  The last sweep adds x' to the
-// unknown component of step a-1.
+// Row i of one preconditioned sweep x' = x + M (b - A x) (x == nullptr:
+// x' = M b), the residual of each row j of M's pattern recomputed on the fly.
+// Shared by the one-sweep and the fused kernels, so both give the same bits.
+template <typename LDX>
+__device__ __forceinline__ double sai_row_sweep(int i, int ns, int W, int ell_w, const double *__restrict__ mval,
+                                                const int32_t *__restrict__ mcol, const double *__restrict__ aoff,
+                                                const int32_t *__restrict__ acol, const double *__restrict__ ainv,
+                                                const double *__restrict__ b, const double *x, LDX ldx)
+{
+    double s = x ? ldx(x + i) : 0.0;
+    for (int k = 0; k < W; ++k) {
+        int j = mcol[(int64_t)k * ns + i];
+        if (j < 0) continue;
+        double r = b[j];
+        if (x) {
+            r -= ldx(x + j) / ainv[j];
+            for (int e = 0; e < ell_w; ++e) {
+                int l = acol[(int64_t)e * ns + j];
+                if (l >= 0) r -= aoff[(int64_t)e * ns + j] * ldx(x + l);
+            }
+        }
+        s += mval[(int64_t)k * ns + i] * r;
+    }
+    return s;
+}
+
+// The last sweep adds x' to the unknown component of step a-1 and flags a
+// non-finite value (flag bit 1).
+__device__ __forceinline__ void sai_store(int i, double s, int64_t row, const int8_t *__restrict__ phi, double *u,
+                                          double *q, float2 *us, float2 *qs, const int32_t *__restrict__ hpos,
+                                          int *flag)
+{
+    double *hh = phi[i] ? u : q;
+    double v = hh[row + i] + s;
+    hh[row + i] = v;
+    if (us) {
+        float hi = __double2float_rn(v);
+        (phi[i] ? us : qs)[row + (hpos ? hpos[i] : i)] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+    if (!isfinite(s)) atomicOr(flag, 1);
+}
+
+// One preconditioned sweep per launch.
 __global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__ mval, const int32_t *__restrict__ mcol,
                             const double *__restrict__ aoff, const int32_t *__restrict__ acol,
                             const double *__restrict__ ainv, const double *__restrict__ b,
@@ -247,31 +303,38 @@ __global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
-    double s = x ? x[i] : 0.0;
-    for (int k = 0; k < W; ++k) {
-        int j = mcol[(int64_t)k * ns + i];
-        if (j < 0) continue;
-        double r = b[j];
-        if (x) {
-            r -= x[j] / ainv[j];
-            for (int e = 0; e < ell_w; ++e) {
-                int l = acol[(int64_t)e * ns + j];
-                if (l >= 0) r -= aoff[(int64_t)e * ns + j] * x[l];
-            }
-        }
-        s += mval[(int64_t)k * ns + i] * r;
-    }
-    if (last) {
-        double *hh = phi[i] ? u : q;
-        double v = hh[row + i] + s;
-        hh[row + i] = v;
-        if (us) {
-            float hi = __double2float_rn(v);
-            (phi[i] ? us : qs)[row + (hpos ? hpos[i] : i)] = make_float2(hi, __double2float_rn(v - (double)hi));
-        }
-        if (!isfinite(s)) atomicOr(flag, 1);
-    } else {
+    const double s = sai_row_sweep(i, ns, W, ell_w, mval, mcol, aoff, acol, ainv, b, x,
+                                   [](const double *p) { return *p; });
+    if (last)
+        sai_store(i, s, row, phi, u, q, us, qs, hpos, flag);
+    else
         xout[i] = s;
+}
+
+// All K sweeps of one step in one cooperative launch (rows grid-strided),
+// a bounded grid barrier between sweeps (x read with ld.global.cg, as in
+// the fused Jacobi solve).
+__global__ void __launch_bounds__(256) k_sai_fused(int ns, int W, int ell_w, const double *__restrict__ mval,
+                                                   const int32_t *__restrict__ mcol, const double *__restrict__ aoff,
+                                                   const int32_t *__restrict__ acol,
+                                                   const double *__restrict__ ainv, const double *__restrict__ b,
+                                                   double *xa, double *xb, int K, int64_t row,
+                                                   const int8_t *__restrict__ phi, double *u, double *q, float2 *us,
+                                                   float2 *qs, const int32_t *__restrict__ hpos, int *flag,
+                                                   unsigned *bar)
+{
+    for (int it = 0; it < K; ++it) {
+        const double *xin = (it == 0) ? nullptr : ((it & 1) ? xa : xb);
+        double *xout = (it & 1) ? xb : xa;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+            const double s = sai_row_sweep(i, ns, W, ell_w, mval, mcol, aoff, acol, ainv, b, xin,
+                                           [](const double *p) { return __ldcg(p); });
+            if (it == K - 1)
+                sai_store(i, s, row, phi, u, q, us, qs, hpos, flag);
+            else
+                xout[i] = s;
+        }
+        if (it < K - 1) grid_barrier(bar, flag);
     }
 }
 
@@ -389,8 +452,9 @@ static int sai_pass(tdbem_sai *S, tdbem_ctx *c, float *loss_host)
     if (!c || !c->prepared || !c->d_aoff) return sai_fail(S, TDBEM_ERR_STATE, "context not prepared");
     cudaMemsetAsync(S->grad, 0, S->nw * sizeof(float), c->s);
     cudaMemsetAsync(S->loss, 0, sizeof(float), c->s);
-    k_sai_train_rows<<<(c->ns + 127) / 128, 128, 0, c->s>>>(c->ns, c->ell_w, S->W, S->H, c->d_aoff, c->d_acol,
-                                                            c->d_ainv, c->d_xc, c->cdt, S->w16, S->grad, S->loss);
+    k_sai_train_rows<<<(c->ns + 127) / 128, 128, (S->nw + 1) * sizeof(float), c->s>>>(
+        c->ns, c->ell_w, S->W, S->H, S->nw, c->d_aoff, c->d_acol, c->d_ainv, c->d_xc, c->cdt, S->w16, S->grad,
+        S->loss);
     if (cudaGetLastError() != cudaSuccess) return sai_fail(S, TDBEM_ERR_CUDA, "training kernel");
     if (loss_host) cudaMemcpyAsync(loss_host, S->loss, sizeof(float), cudaMemcpyDeviceToHost, c->s);
     return TDBEM_OK;
@@ -436,8 +500,8 @@ int tdbem_sai_train(tdbem_sai *S, tdbem_ctx *const *ctxs, int32_t n, int32_t epo
 }
 
 // Installs the learned M as the zero-lag solver of a context when its
-// a-priori sweep count (||I - M A||_inf = q': error <= q'^K) needs fewer
-// kernel launches than Jacobi's; otherwise Jacobi stays (the fallback).
+// a-priori sweep count (||I - M A||_inf = q': error <= q'^K) is below
+// Jacobi's; otherwise Jacobi stays (the fallback).
 // *sweeps receives the sweeps of the solver in use, *contraction its q.
 int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_t *sweeps, double *contraction)
 {
@@ -503,6 +567,14 @@ int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_
         c->sai_w = W;
         c->sai_iters = K;
         c->sai_contraction = qmax;
+        // the K sweeps in one cooperative launch where the device allows it
+        c->sai_grid = 0;
+        int coop = 0, nsm = 0, per = 0;
+        if (c->d_bar && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sai_fused, 256, 0) == cudaSuccess && coop &&
+            per >= 1)
+            c->sai_grid = (int)std::min<int64_t>(((int64_t)ns + 255) / 256, (int64_t)per * nsm);
     }
     if (use_sai) *use_sai = better ? 1 : 0;
     if (sweeps) *sweeps = better ? K : c->solve_iters;
@@ -513,6 +585,18 @@ int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_
 }  // extern "C"
 
 namespace tdbem {
+
+// The SAI-preconditioned zero-lag solve of one step: all K sweeps in one
+// cooperative launch.
+cudaError_t launch_sai_fused(tdbem_ctx *c, int alpha)
+{
+    int ns = c->ns, W = c->sai_w, E = c->ell_w, K = c->sai_iters;
+    int64_t row = (int64_t)(alpha - 1) * ns;
+    void *args[] = {&ns, &W, &E, &c->sai_val, &c->sai_col, &c->d_aoff, &c->d_acol, &c->d_ainv, &c->d_b,
+                    &c->d_xa, &c->d_xb, &K, &row, &c->d_phi, &c->d_u, &c->d_q, &c->d_us, &c->d_qs, &c->d_hpos,
+                    &c->d_flag, &c->d_bar};
+    return cudaLaunchCooperativeKernel((const void *)k_sai_fused, dim3(c->sai_grid), dim3(256), args, 0, c->s);
+}
 
 // The SAI-preconditioned zero-lag solve of one step (sweep it of K).
 cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it)

@@ -12,18 +12,24 @@
 // K-major (each row holds its K values contiguously), so one 128-byte row of
 // a 64-wide K chunk is one swizzle row of the SW128 layout.
 //
-// One CTA per output tile, 6 warps:
+// Persistent: one CTA per SM, each taking tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...; 6 warps:
 //   warp 0 (one thread): TMA producer; per K chunk it loads every term's
 //     128 x 64 A tile and BN x 64 B tile into a ring of shared-memory stages
-//     (cp.async.bulk.tensor, 128-byte swizzle, completion on an mbarrier);
-//   warp 1: allocates BN TMEM columns; one thread issues tcgen05.mma
-//     (M = 128, N = BN, K = 16, FP32 accumulate in TMEM) for every product
-//     and K step of a stage, then tcgen05.commit frees the stage;
-//   warps 2-5: epilogue; each reads its 32 TMEM lanes (tcgen05.ld 32x32b)
-//     and stores the FP32 results, one coalesced 128-byte row per column.
+//     (cp.async.bulk.tensor, 128-byte swizzle, completion on an mbarrier),
+//     running ahead across tile boundaries;
+//   warp 1: allocates 2 BN TMEM columns (two accumulators); one thread
+//     issues tcgen05.mma (M = 128, N = BN, K = 16, FP32 accumulate in TMEM)
+//     for every product and K step of a stage, tcgen05.commit frees the
+//     stage, and a commit per tile hands the accumulator to the epilogue;
+//   warps 2-5: epilogue; each reads its 32 TMEM lanes (tcgen05.ld 32x32b),
+//     returns the accumulator to the MMA warp and stores the FP32 results,
+//     one coalesced 128-byte row per column, while the MMAs of the next
+//     tile run in the other accumulator.
 // Every mbarrier wait gives up after kWaitNs of global time, sets bit 3 of
 // *err and lets the CTA finish: TMA copies in flight are waited for (with
-// the same bound) and the TMEM columns are freed before the CTA exits.
+// the same bound), the MMAs issued are drained and the TMEM columns are
+// freed before the CTA exits.
 #include <cuda.h>
 
 #include <algorithm>
@@ -53,6 +59,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
@@ -142,28 +153,36 @@ template <int BN>
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcGemmArgs g)
 {
+    // graph-replayed steps: the whole grid leaves before touching shared
+    // memory or TMEM when this step has no M2L at the GEMM's level
+    if (g.when.alpha && when_interval(g.when) < 0) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr uint32_t kATile = kTcBM * 128, kBTile = BN * 128;
     const uint32_t stage_bytes = g.nta * kATile + g.ntb * kBTile;
     const int nstage = g.nstage;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)nstage * stage_bytes);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + nstage), accf = smem_u32(bars + 2 * nstage);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * nstage + 1);
+    // full[s], empty[s]; accumulator full[2] / empty[2]; MMA drain
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + nstage), accf0 = smem_u32(bars + 2 * nstage),
+                   acce0 = smem_u32(bars + 2 * nstage + 2), drain = smem_u32(bars + 2 * nstage + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * nstage + 5);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const TcTile t = g.tiles[blockIdx.x];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nstage; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 4);  // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)BN)
+                     "r"((uint32_t)(2 * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -172,82 +191,112 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int K = g.kchunks;
+    const int ntiles = g.ntiles;
 
     if (warp == 0) {
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-            int issued = 0;
-            for (int kc = 0; kc < K; ++kc) {
-                const int s = kc % nstage;
-                if (kc >= nstage && !mbar_wait(empty0 + 8 * s, ((kc / nstage) - 1) & 1)) {
-                    atomicOr(g.err, 8);
-                    break;
+            int it = 0;  // K chunks issued by this CTA
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const TcTile t = g.tiles[tile];
+                for (int kc = 0; kc < K; ++kc, ++it) {
+                    const int s = it % nstage;
+                    if (it >= nstage && !mbar_wait(empty0 + 8 * s, ((it / nstage) - 1) & 1)) {
+                        atomicOr(g.err, 8);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+                    mbar_expect_tx(full0 + 8 * s, stage_bytes);
+                    for (int a = 0; a < g.nta; ++a)
+                        tma_load_2d(st + a * kATile, &tmA, kc * kTcBK, t.a_row + a * g.a_term_rows, full0 + 8 * s);
+                    for (int b = 0; b < g.ntb; ++b)
+                        tma_load_2d(st + g.nta * kATile + b * kBTile, &tmB, kc * kTcBK, t.b_row + b * g.b_term_rows,
+                                    full0 + 8 * s);
                 }
-                const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
-                mbar_expect_tx(full0 + 8 * s, stage_bytes);
-                for (int a = 0; a < g.nta; ++a)
-                    tma_load_2d(st + a * kATile, &tmA, kc * kTcBK, t.a_row + a * g.a_term_rows, full0 + 8 * s);
-                for (int b = 0; b < g.ntb; ++b)
-                    tma_load_2d(st + g.nta * kATile + b * kBTile, &tmB, kc * kTcBK, t.b_row + b * g.b_term_rows,
-                                full0 + 8 * s);
-                issued = kc + 1;
             }
             // every copy issued has landed before the CTA may exit
-            for (int kc = (issued > nstage ? issued - nstage : 0); kc < issued; ++kc)
-                if (!mbar_wait(full0 + 8 * (kc % nstage), (kc / nstage) & 1)) atomicOr(g.err, 8);
+            for (int k = (it > nstage ? it - nstage : 0); k < it; ++k)
+                if (!mbar_wait(full0 + 8 * (k % nstage), (k / nstage) & 1)) atomicOr(g.err, 8);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = f16_idesc(g.fmt, kTcBM, BN);
-            for (int kc = 0; kc < K; ++kc) {
-                const int s = kc % nstage;
-                if (!mbar_wait(full0 + 8 * s, (kc / nstage) & 1)) {
+            int it = 0, j = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++j) {
+                const int b = j & 1;
+                // the epilogue has read this accumulator's previous tile
+                if (j >= 2 && !mbar_wait(acce0 + 8 * b, ((j >> 1) - 1) & 1)) {
                     atomicOr(g.err, 8);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
-                for (int p = 0; p < g.nprod; ++p) {
-                    const uint64_t da = sw128_desc(st + (g.prod[p] >> 4) * kATile);
-                    const uint64_t db = sw128_desc(st + g.nta * kATile + (g.prod[p] & 15) * kBTile);
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int kc = 0; kc < K; ++kc, ++it) {
+                    const int s = it % nstage;
+                    if (!mbar_wait(full0 + 8 * s, (it / nstage) & 1)) {
+                        atomicOr(g.err, 8);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+                    for (int p = 0; p < g.nprod; ++p) {
+                        const uint64_t da = sw128_desc(st + (g.prod[p] >> 4) * kATile);
+                        const uint64_t db = sw128_desc(st + g.nta * kATile + (g.prod[p] & 15) * kBTile);
 #pragma unroll
-                    for (int kk = 0; kk < kTcBK / 16; ++kk)
-                        tc_mma(tmem, da + 2 * kk, db + 2 * kk, idesc, (kc | p | kk) != 0);
+                        for (int kk = 0; kk < kTcBK / 16; ++kk)
+                            tc_mma(d, da + 2 * kk, db + 2 * kk, idesc, (kc | p | kk) != 0);
+                    }
+                    tc_commit(empty0 + 8 * s);
                 }
-                tc_commit(empty0 + 8 * s);
+                if (ok) tc_commit(accf0 + 8 * b);
             }
-            tc_commit(accf);
+            // every MMA issued has completed before the columns are freed
+            tc_commit(drain);
+            if (!mbar_wait(drain, 0)) atomicOr(g.err, 8);
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 of
+        // the tile's accumulator, then hands the columns back to the MMA
+        // warp, so the next-but-one tile's MMAs overlap these stores
         const int q = warp & 3, row = 32 * q + lane;
-        const bool ok = mbar_wait(accf, 0);
-        tc_fence_after();
-        if (!ok) {
-            if (lane == 0) atomicOr(g.err, 8);
-        } else {
+        int j = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+            const int b = j & 1;
+            // warp-uniform decision: the TMEM loads below are .sync.aligned
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, (j >> 1) & 1));
+            tc_fence_after();
+            if (!ok) {
+                if (lane == 0) atomicOr(g.err, 8);
+                break;
+            }
+            const TcTile t = g.tiles[tile];
+            float *out = g.C + t.c_off + row;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c0), r);
                 if (row < t.rows) {
-                    float *out = g.C + t.c_off + row;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c0 + j < t.cols) out[(int64_t)(c0 + j) * g.ldc] = __uint_as_float(r[j]);
+                    for (int x = 0; x < 32; ++x)
+                        if (c0 + x < t.cols) out[(int64_t)(c0 + x) * g.ldc] = __uint_as_float(r[x]);
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        // the accumulator is complete (or its wait gave up) before the columns are freed
-        if (lane == 0 && !mbar_test(accf, 0)) mbar_wait(accf, 0);
-        __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                     : "memory");
     }
 }
 
@@ -297,7 +346,7 @@ int tc_stages(int nta, int ntb, int bn)
 
 size_t tc_smem_bytes(int nta, int ntb, int bn, int nstage)
 {
-    return 1024 + (size_t)nstage * (nta * kTcBM * 128 + ntb * bn * 128) + 8 * (2 * nstage + 1) + 16;
+    return 1024 + (size_t)nstage * (nta * kTcBM * 128 + ntb * bn * 128) + 8 * (2 * nstage + 5) + 16;
 }
 
 cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const TcGemmArgs &a, int ntiles, int bn,
@@ -311,15 +360,27 @@ cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const T
         if ((a.prod[p] >> 4) >= a.nta || (a.prod[p] & 15) >= a.ntb) return cudaErrorInvalidValue;
     const size_t shm = tc_smem_bytes(a.nta, a.ntb, bn, a.nstage);
     if (shm > (size_t)kTcSmemBudget) return cudaErrorInvalidValue;
+    // persistent: one CTA per SM (the shared-memory ring fills the SM), each
+    // taking every gridDim-th tile
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaError_t e0 = cudaGetDevice(&dev);
+        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e0 != cudaSuccess || nsm < 1) return e0 != cudaSuccess ? e0 : cudaErrorInvalidValue;
+    }
+    TcGemmArgs g = a;
+    g.ntiles = ntiles;
+    const int grid = std::min(ntiles, nsm);
     cudaError_t e;
     if (bn == 128) {
         e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBudget);
         if (e != cudaSuccess) return e;
-        k_tc_gemm<128><<<ntiles, 192, shm, s>>>(ta, tb, a);
+        k_tc_gemm<128><<<grid, 192, shm, s>>>(ta, tb, g);
     } else if (bn == 256) {
         e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBudget);
         if (e != cudaSuccess) return e;
-        k_tc_gemm<256><<<ntiles, 192, shm, s>>>(ta, tb, a);
+        k_tc_gemm<256><<<grid, 192, shm, s>>>(ta, tb, g);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -50,6 +50,64 @@ struct Tree {
     std::vector<TreeLevel> levels;
 };
 
+// Graph-replayed steps (tdbem_step_graph, tdbem_batch_*): every kernel of
+// the far field reads the step alpha from the device counter and works out
+// there whether its pass runs at this step and for which interval (the host
+// decides both in plain stepping).  A boundary step is the first step of a
+// leaf interval: alpha - 1 = k1 Lt, k1 >= 1 leaf intervals completed.
+struct StepWhen {
+    const int *alpha = nullptr;  // device step counter; nullptr: plain stepping
+    int alim = 0;                // last step, Nt - 1
+    int lt = 1;                  // steps per leaf interval
+    int span = 1;                // leaf intervals per interval of the pass's level
+};
+
+// The index of the level's interval that ended just before this step, or -1
+// when the pass does not run at this step.
+__device__ __forceinline__ int when_interval(const StepWhen w)
+{
+    const int a = *w.alpha;
+    if (a > w.alim || a < 2 || (a - 1) % w.lt) return -1;
+    const int k1 = (a - 1) / w.lt;
+    if (k1 % w.span) return -1;
+    return k1 / w.span - 1;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): arrival
+// counter bar[0], generation bar[1].  The wait is bounded: after
+// kBarrierPolls polls the CTA records a timeout (flag bit 4) and goes on,
+// so a barrier that cannot complete ends the kernel with an error that the
+// host reports, never with a hang.
+constexpr unsigned kBarrierPolls = 1u << 22;  // with 64 ns sleeps: about 0.3 s
+
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            // poll with short sleeps (polling without them measured slower:
+            // every waiting CTA then hammers the same word)
+            unsigned polls = 0;
+            while (*gen == g) {
+                if (++polls > kBarrierPolls) {
+                    atomicOr(flag, 4);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // Split-precision tensor-core GEMM (tc_gemm.cu): one output tile of at most
 // 128 rows (A rows) x BN columns (B rows), C[c_off + j ldc + i].
 constexpr int kTcBM = 128;
@@ -75,7 +133,9 @@ struct TcGemmArgs {
     int64_t ldc;
     float *C;
     const TcTile *tiles;
+    int32_t ntiles;
     int *err;                         // bit 3 (value 8) is set when a pipeline wait gave up
+    StepWhen when;                    // graph-replayed steps: run only at the level's M2L steps
 };
 
 cudaError_t tc_make_map(CUtensorMap *map, const void *base, int64_t rows, int kp, int box_rows);
@@ -113,24 +173,25 @@ struct FmmLevel {
     int32_t *pS = nullptr;       // [np] source cell of each column
     uint8_t *pg = nullptr;       // [np] symmetry element of each column
     uint8_t *pc = nullptr;       // [np] class of each column
-    void *kr = nullptr;          // [ncls][d][P3][P3] r_ab^(e-1) between the canonical nodes (e = 0..d-1;
+    void *kr = nullptr;          // [ncls][d+1][P3][P3] r_ab^(e-1) between the canonical nodes (e = 0..d;
                                  // e = 1 unused): FP64, or float pairs in the tensor-core forms
-    void *dmu = nullptr;         // [np][d][P3] time moments of the columns (derivative rows)
-    void *dF = nullptr;          // [np][d][d][P3] their distance-power products
-    double *dss = nullptr;       // [np][d] sums of the time moments
+    void *dmu = nullptr;         // [np][d+1][P3] time moments of the columns (exact rows: the block
+                                 // L_{k+mu+1,k} and the derivative rows)
+    void *dF = nullptr;          // [np][d+1][d+1][P3] their distance-power products
+    double *dss = nullptr;       // [np][d+1] sums of the time moments
     int4 *djobs = nullptr;       // [njobs] (class, first column, columns) of the products kernel
-    double *dcoef = nullptr;     // [d][pt][d][d] binomial-expansion coefficients of the derivative rows
+    double *dcoef = nullptr;     // [d+1][pt][d+1][d+1] binomial-expansion coefficients of the exact rows
     int njobs = 0;
     int64_t *ooff = nullptr;     // [nc+1] columns of each observation cell (CSR)
     int64_t *oidx = nullptr;     // [np] their columns, in interaction-list order
     uint8_t *og = nullptr;       // [np] their symmetry elements
-    double *op = nullptr;        // FP64 form: [ncls][(mu+1+d) P][P] canonical operator stacks
+    double *op = nullptr;        // FP64 form: [ncls][mu P][P] canonical operator stacks (near future 1..mu)
     double *Bbuf = nullptr;      // FP64 form: [np][P] gathered (permuted) moments
-    double *Cbuf = nullptr;      // FP64 form: [np][(mu+1+d) P] products
+    double *Cbuf = nullptr;      // FP64 form: [np][mu P] products
     // tensor-core forms: split terms of operators and moments, FP32 products
     uint16_t *opt = nullptr;     // [nta][ncls][Rp][Kp] BF16 operator terms
     uint16_t *Bt = nullptr;      // [ntb][np][Kp] BF16 moment terms
-    float *C32 = nullptr;        // [np][(mu+1+d) P] products
+    float *C32 = nullptr;        // [np][mu P] products
     TcTile *tiles = nullptr;     // [ntiles] GEMM tiles (zero operator blocks skipped)
     int ntiles = 0;
     int tile_n = 128;            // tile width chosen by the setup-time tuner
@@ -144,7 +205,7 @@ struct Fmm {
     bool on = false;
     struct cublasContext *blas = nullptr;  // cuBLAS handle (FP64 form)
     int L = 0, ps = 0, pt = 0, P3 = 0, P = 0, mu = 0, Lt = 0, nblk = 0, nd = 0, nslot = 0;
-    int ngb = 0;                            // operator blocks applied as GEMMs (near future, mu + 1)
+    int ngb = 0;                            // operator blocks applied as GEMMs (near future 1..mu)
     int R = 0, Rp = 0, Kp = 0;              // their rows ngb P, rows padded to 128, K padded to 64
     int nta = 0, ntb = 0, nprod = 0;        // tensor-core forms: split terms and products
     int prod[kTcMaxProd] = {0};
@@ -157,7 +218,6 @@ struct Fmm {
     double *wk = nullptr;                   // [d+2] w^{kappa,d}
     double *Tm = nullptr;                   // [2][pt][pt] time transfer
     double *wt = nullptr;                   // [pt] Chebyshev time nodes
-    double *cmp = nullptr;                  // c_m^p(k) of the current call
     double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
     int far_k = -1;                         // leaf interval the far field belongs to
 };
@@ -246,6 +306,7 @@ struct tdbem_ctx {
     double *sai_val = nullptr;   // [sai_w][ns]
     int32_t *sai_col = nullptr;  // [sai_w][ns]
     int sai_w = 0, sai_iters = 0;
+    int sai_grid = 0;            // CTAs of the fused SAI launch (0: one launch per sweep)
     double sai_contraction = 0.0;
     double *d_r = nullptr;       // [ns] residual
     int *d_alpha = nullptr;      // device-side step counter for graph-replayed steps
@@ -284,7 +345,7 @@ cudaError_t build_near_lists(tdbem_ctx *c);
 
 // Space-time FMM (fmm.cu)
 cudaError_t fmm_setup(tdbem_ctx *c, std::string &why);
-cudaError_t fmm_boundary(tdbem_ctx *c, int k);
+cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph = false);
 // Phase timer hooks for fmm.cu (events on the context's stream).
 void phase_begin(tdbem_ctx *c, cudaEvent_t *e);
 void phase_end(tdbem_ctx *c, int phase, cudaEvent_t e);
@@ -299,6 +360,7 @@ cudaError_t launch_jacobi_fused(tdbem_ctx *c, int alpha);
 cudaError_t launch_gather_x(tdbem_ctx *c, int a0, int nsteps, double *x);
 cudaError_t launch_alpha_next(tdbem_ctx *c);
 cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it);
+cudaError_t launch_sai_fused(tdbem_ctx *c, int alpha);
 cudaError_t launch_split_coefficients(tdbem_ctx *c);
 cudaError_t launch_split_histories(tdbem_ctx *c);
 

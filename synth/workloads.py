@@ -73,6 +73,21 @@ def workload(name, nt=None):
         xyz, tri = icosphere(subdiv)
         w = Workload(name, xyz, tri, c, 0.5 * mean_edge(xyz, tri) / c, 64, d,
                      parts[1], parts[3], "uniform", sigma=0.5)
+    elif name.startswith("sphere") and "_plane" in name and name != "sphere5120_bmbie_d1_soft_plane":
+        # icospheres (radius 1) under the seeded Gaussian plane pulse, e.g. the
+        # 81920-element sphere sphere81920_bmbie_d2_hard_plane
+        parts = name.split("_")
+        ns = int(parts[0][len("sphere"):])
+        subdiv = {80: 1, 320: 2, 1280: 3, 5120: 4, 20480: 5, 81920: 6}[ns]
+        seed = int(parts[-1][1:]) if parts[-1].startswith("s") else 0
+        xyz, tri = icosphere(subdiv)
+        rng = np.random.default_rng(seed)
+        sig = 0.3
+        bc = {"hard": "neumann", "soft": "dirichlet"}[parts[3]]
+        w = Workload(name, xyz, tri, c, 0.5 * mean_edge(xyz, tri) / c, 2048, int(parts[2][1:]),
+                     parts[1], bc, "plane", sigma=sig,
+                     t0=4 * sig + float(np.linalg.norm(xyz, axis=1).max()) / c,
+                     direction=_unit(rng))
     elif name == "sphere5120_bmbie_d1_soft_plane":
         xyz, tri = icosphere(4)
         rng = np.random.default_rng(2)

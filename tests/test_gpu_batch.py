@@ -2,7 +2,8 @@
 identical (bit for bit) to plain stepping: the same kernels on the same
 data, only launched from a captured CUDA graph, and for the batch from one
 graph in which each instance is an independent branch.  Instances differ in
-mesh size, B-spline order, BIE, boundary condition and precision."""
+mesh size, B-spline order, BIE, boundary condition, precision, Nt and
+algorithm (direct path or space-time FMM)."""
 
 import numpy as np
 import pytest
@@ -82,7 +83,9 @@ def test_batch_equals_each_instance_alone():
             s.close()
 
 
-def test_batch_rejects_fmm_and_duplicates():
+def test_batch_rejects_fp64_fmm_and_duplicates():
+    """The FP64 FMM form's GEMMs are library calls that cannot read the
+    device-side step, so its steps are not graph-replayed."""
     _need_gpu()
     from paper_2111_05205_gb300 import abi
     w = case("ellipsoid320_bmbie_d2_hard_plane_s7", nt=10)
@@ -98,6 +101,88 @@ def test_batch_rejects_fmm_and_duplicates():
     finally:
         f.close()
         d.close()
+
+
+# FMM instances: depth 3 crosses leaf boundaries every Lt steps and level-2
+# boundaries every 2 Lt; the 81-step runs reach the distant-future
+# recurrence of Formula 1
+FMM_CASES = [
+    ("sphere1280_bmbie_d2_neumann_uniform", 3, (2, 2, 0), 1, 81),
+    ("sphere1280_bmbie_d1_dirichlet_uniform", 3, (3, 3, 0), 2, 40),
+    ("ellipsoid320_bmbie_d2_hard_plane_s7", 2, (3, 3, 0), 1, 37),
+]
+
+
+@pytest.mark.parametrize("name,L,fmm,precision,nt", FMM_CASES)
+def test_graph_fmm_steps_equal_plain_steps(name, L, fmm, precision, nt):
+    """FMM steps replayed from one captured graph (every far-field kernel
+    decides on the device whether this step is one of its boundaries) give
+    the same history, bit for bit, as plain stepping, including plain steps
+    before and after graph steps."""
+    _need_gpu()
+    from paper_2111_05205_gb300 import abi
+    w = case(name, nt=nt)
+    a = gpu_solver(w, precision=precision, depth=L, fmm=fmm)
+    b = gpu_solver(w, precision=precision, depth=L, fmm=fmm)
+    try:
+        n = nt - 1
+        abi.tdbem_step(a.ctx, n)
+        abi.tdbem_step(b.ctx, 5)           # plain, then graph, then plain
+        abi.tdbem_step_graph(b.ctx, n - 12)
+        abi.tdbem_step(b.ctx, 4)
+        abi.tdbem_step_graph(b.ctx, 3)
+        assert abi.tdbem_steps_done(b.ctx) == n
+        ua, qa = a.solution(0, n)
+        ub, qb = b.solution(0, n)
+        assert np.abs(ua).max() + np.abs(qa).max() > 0
+        assert np.array_equal(ua, ub) and np.array_equal(qa, qb)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_batch_with_fmm_instances_of_uneven_nt():
+    """FMM and direct instances of different meshes, orders, BIEs,
+    precisions and Nt in one batch graph: each history equals the instance
+    stepped alone (bit for bit)."""
+    _need_gpu()
+    from paper_2111_05205_gb300 import abi
+    spec = [("sphere1280_bmbie_d2_neumann_uniform", 1, 3, (2, 2, 0), 81),
+            ("ellipsoid80_bmbie_d2_hard_plane_s7", 1, 0, None, 30),
+            ("sphere1280_bmbie_d1_dirichlet_uniform", 3, 3, (3, 3, 0), 52),
+            ("ellipsoid320_bmbie_d2_hard_plane_s7", 1, 2, (3, 3, 0), 37)]
+    ws = [case(n, nt=nt) for n, _, _, _, nt in spec]
+
+    def make(w, prec, L, fmm):
+        return gpu_solver(w, precision=prec, depth=L, fmm=fmm) if fmm else gpu_solver(w, precision=prec)
+
+    ref = []
+    for w, (n, prec, L, fmm, nt) in zip(ws, spec):
+        s = make(w, prec, L, fmm)
+        try:
+            abi.tdbem_step(s.ctx, nt - 1)
+            ref.append(s.solution(0, nt - 1))
+        finally:
+            s.close()
+    sols = [make(w, prec, L, fmm) for w, (n, prec, L, fmm, nt) in zip(ws, spec)]
+    try:
+        # 8 steps of every instance per graph launch (and single steps for
+        # the remainders)
+        B = abi.tdbem_batch_create_steps([s.ctx for s in sols], 8)
+        try:
+            abi.tdbem_batch_step(B, 9)
+            abi.tdbem_batch_step(B, 40)
+            abi.tdbem_batch_step(B, 100)
+            abi.tdbem_batch_sync(B)
+        finally:
+            abi.tdbem_batch_destroy(B)
+        for s, r, (n, prec, L, fmm, nt) in zip(sols, ref, spec):
+            assert abi.tdbem_steps_done(s.ctx) == nt - 1
+            u, q = s.solution(0, nt - 1)
+            assert np.array_equal(u, r[0]) and np.array_equal(q, r[1]), n
+    finally:
+        for s in sols:
+            s.close()
 
 
 def test_batch_of_uneven_nt():

@@ -6,9 +6,9 @@
    1e-3 relative (FP32 accumulation over the rows).
 2. After training on the GPU on zero-lag matrices assembled by the library
    from seeded random ellipsoids, the learned M solves the zero-lag system
-   of a held-out mesh in fewer sweeps (one launch each) than Jacobi, by the
-   a-priori bound of ||I - M A||_inf, and the marching solution equals the
-   Jacobi one (1e-12: both solve to 1e-16).
+   of a held-out mesh in fewer sweeps than Jacobi, by the a-priori bound of
+   ||I - M A||_inf, all of them in one cooperative launch per step, and the
+   marching solution equals the Jacobi one (1e-12: both solve to 1e-16).
 """
 
 import numpy as np
@@ -78,6 +78,11 @@ def test_learned_sai_beats_jacobi_on_a_held_out_mesh():
             ua, _ = a.solution()
             ub, _ = b.solution()
             assert np.linalg.norm(ua - ub) <= 1e-12 * np.linalg.norm(ua)
+            # the installed SAI's sweeps are reported, all K of a step in one
+            # cooperative launch
+            st = b.stats()
+            assert st["solve_iters"] == sweeps and abs(st["solve_contraction"] - q) <= 1e-12
+            assert st["launches_solve"] == 29
         finally:
             a.close()
             b.close()

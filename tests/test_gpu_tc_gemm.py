@@ -39,6 +39,10 @@ def _split(x, nterm, fmt):
     (333, 77, 648, 3, 3, [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)], 1, 128),
     (130, 520, 256, 2, 2, [(0, 0), (0, 1), (1, 0)], 1, 256),
     (257, 129, 200, 2, 2, [(0, 0), (0, 1), (1, 0)], 0, 128),
+    # more tiles than SMs: each persistent CTA takes several tiles, both
+    # TMEM accumulators and the ring's phases wrap across tile boundaries
+    (2600, 2700, 192, 2, 2, [(0, 0), (0, 1), (1, 0)], 1, 128),
+    (1300, 6000, 100, 1, 1, [(0, 0)], 1, 256),
 ])
 def test_tc_gemm_matches_numpy(m, n, k, nta, ntb, prod, fmt, bn):
     from paper_2111_05205_gb300 import abi, build
