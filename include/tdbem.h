@@ -70,11 +70,19 @@ typedef struct {
     int32_t algo;         /* 0 = direct history sum over all element pairs (Eq. linear);
                              1 = near pairs (leaf neighbours) direct + the far part by the
                              interpolation-based space-time FMM (Sections 3-4, Formula 1) */
-    int32_t precision;    /* 0 = FP64 throughout; 1 = split: the history sum stores every
+    int32_t precision;    /* 0 = FP64 throughout; 1..4 = split: the history sum stores every
                              coefficient and history value as an FP32 pair (hi, lo) (48
                              significant bits) and sums in double-float arithmetic on the
                              FP32 pipes; coefficients, the zero-lag matrix and the solve
-                             are computed in FP64 either way */
+                             are computed in FP64 either way.  The FMM's near-future M2L
+                             blocks run on the tensor cores (FP32 accumulation) with
+                             operators and moments split into 16-bit terms: 1 = three BF16
+                             terms, six products (FP32-grade); 2 = BF16x3 (two terms,
+                             three products); 3 = one BF16 product; 4 = two FP16 terms
+                             scaled by powers of two per operator row and per cell's
+                             moment, three products (about 22 bits).  The last near-future
+                             block, the derivative rows and the recurrence of Formula 1
+                             stay FP64 / double-float in every form. */
     int32_t ps, pt;       /* FMM: interpolation points per space / time dimension (2..8,
                              ps^3 pt <= 4096) */
     int32_t mu;           /* FMM: near-future intervals (Section 4.2); 0 = the smallest value

@@ -28,6 +28,7 @@
 
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "tdbem_internal.cuh"
 
@@ -191,54 +192,55 @@ namespace tdbem {
 //                   (At[j][b] tau_j^sigma - As[j][b] sigma_j^sigma) ell_n(t_sigma),
 // with tau, sigma the folded histories of Eq. tau / Eq. sigma.  The sum over
 // sigma does not involve the spatial node b, so it is taken first, once per
-// (element, temporal node): Tq[j][n] = sum_sigma tau_j^sigma ell_n(t_sigma)
-// (Tu likewise with sigma_j), staged in shared memory for kP2MChunk
-// elements at a time; then M[b + P3 n] += pref sum_j (At Tq - As Tu).
-constexpr int kP2MChunk = 32;
-
-__global__ void k_p2m(int P3, int P, int Lt, int k, int d, int ns, int smax_hist, const int32_t *__restrict__ cstart,
-                      const int32_t *__restrict__ perm, const double *__restrict__ At, const double *__restrict__ As,
-                      const double *__restrict__ q, const double *__restrict__ u, const double *__restrict__ wk,
-                      const double *__restrict__ tl, double pref, double *M, StepWhen w)
+// (element, temporal node) by k_p2m_time: Tq[p][n] = sum_sigma tau_j^sigma
+// ell_n(t_sigma) (Tu likewise with sigma_j), j = perm[p] the element at
+// sorted position p; then k_p2m_moments forms every entry of every leaf
+// cell's moment, one thread per entry:
+// M[c][b + P3 n] += pref sum_{p in c} (At[j][b] Tq[p][n] - As[j][b] Tu[p][n]).
+__global__ void k_p2m_time(int ns, int pt, int Lt, int k, int d, int smax_hist, const int32_t *__restrict__ perm,
+                           const double *__restrict__ q, const double *__restrict__ u, const double *__restrict__ wk,
+                           const double *__restrict__ tl, double *Tq, double *Tu, StepWhen w)
 {
     if (w.alpha && (k = when_interval(w)) < 0) return;
-    __shared__ double Tq[kP2MChunk][8], Tu[kP2MChunk][8];
-    __shared__ int jj[kP2MChunk];
-    const int c = blockIdx.x, pt = P / P3;
-    const int e0 = cstart[c], e1 = cstart[c + 1];
-    for (int base = e0; base < e1; base += kP2MChunk) {
-        const int nj = min(kP2MChunk, e1 - base);
-        for (int x = threadIdx.x; x < nj * pt; x += blockDim.x) {
-            const int jl = x / pt, n = x % pt;
-            const int j = perm[base + jl];
-            double tq = 0.0, tu = 0.0;
-            for (int t = 0; t < Lt; ++t) {
-                const int sg = k * Lt + t;
-                if (sg > smax_hist) break;
-                double tau = 0.0, sig = 0.0;
-                for (int kk = 0; kk <= d + 1 && kk <= sg; ++kk) {
-                    tau += wk[kk] * q[(int64_t)(sg - kk) * ns + j];
-                    sig += wk[kk] * u[(int64_t)(sg - kk) * ns + j];
-                }
-                tq += tau * tl[t * 8 + n];
-                tu += sig * tl[t * 8 + n];
-            }
-            Tq[jl][n] = tq;
-            Tu[jl][n] = tu;
-            if (n == 0) jj[jl] = j;
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= (int64_t)ns * pt) return;
+    const int p = (int)(x / pt), n = (int)(x % pt);
+    const int j = perm[p];
+    double tq = 0.0, tu = 0.0;
+    for (int t = 0; t < Lt; ++t) {
+        const int sg = k * Lt + t;
+        if (sg > smax_hist) break;
+        double tau = 0.0, sig = 0.0;
+        for (int kk = 0; kk <= d + 1 && kk <= sg; ++kk) {
+            tau += wk[kk] * q[(int64_t)(sg - kk) * ns + j];
+            sig += wk[kk] * u[(int64_t)(sg - kk) * ns + j];
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < P; e += blockDim.x) {
-            const int b = e % P3, n = e / P3;
-            double acc = 0.0;
-            for (int jl = 0; jl < nj; ++jl) {
-                const int64_t r = (int64_t)jj[jl] * P3 + b;
-                acc += At[r] * Tq[jl][n] - As[r] * Tu[jl][n];
-            }
-            M[(int64_t)c * P + e] += pref * acc;
-        }
-        __syncthreads();
+        tq += tau * tl[t * 8 + n];
+        tu += sig * tl[t * 8 + n];
     }
+    Tq[x] = tq;
+    Tu[x] = tu;
+}
+
+// One thread per moment entry e = b + P3 n of leaf cell c (grid: cells x
+// ceil(P / 256)).
+__global__ void k_p2m_moments(int P3, int P, const int32_t *__restrict__ cstart, const int32_t *__restrict__ perm,
+                              const double *__restrict__ At, const double *__restrict__ As,
+                              const double *__restrict__ Tq, const double *__restrict__ Tu, double pref, double *M,
+                              StepWhen w)
+{
+    if (w.alpha && when_interval(w) < 0) return;
+    const int c = blockIdx.x;
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= P) return;
+    const int pt = P / P3, b = e % P3, n = e / P3;
+    const int p0 = cstart[c], p1 = cstart[c + 1];
+    double acc = 0.0;
+    for (int p = p0; p < p1; ++p) {
+        const int64_t r = (int64_t)perm[p] * P3 + b;
+        acc += At[r] * Tq[(int64_t)p * pt + n] - As[r] * Tu[(int64_t)p * pt + n];
+    }
+    M[(int64_t)c * P + e] += pref * acc;
 }
 
 // One mode product of a separable transfer on a [ps, ps, ps, pt] tensor:
@@ -510,6 +512,89 @@ __global__ void k_split_operators(int ncls, int R, int P, int Rp, int Kp, int nt
         uint16_t t[kTcMaxTerms];
         split_bf16(op[e], nterm, t);
         for (int k = 0; k < nterm; ++k) opt[(((int64_t)k * ncls + c) * Rp + row) * Kp + col] = t[k];
+    }
+}
+
+// Scaled FP16 form (precision 4): x = 2^e (h_0 + h_1) with h_0 = fp16(x 2^-e),
+// h_1 = fp16(x 2^-e - h_0); the power of two puts the largest |entry| of a
+// row (operators) or of a cell's moment (moments) in [2^13, 2^14), within
+// FP16's range, so the two terms carry about 22 significant bits of every
+// entry near that maximum.  The scales leave the GEMM's FP32 accumulation
+// exact in exponent and are applied in its epilogue.
+__device__ __forceinline__ int f16_exp(double m)
+{
+    return m > 0.0 ? ilogb(m) - 13 : 0;
+}
+
+__device__ __forceinline__ void split_f16(double x, uint16_t *t)
+{
+    const __half h0 = __double2half(x);
+    t[0] = __half_as_ushort(h0);
+    t[1] = __half_as_ushort(__double2half(x - (double)__half2float(h0)));
+}
+
+// Operator terms of the scaled FP16 form: one warp per operator row
+// (class c, row < R): its largest |entry|, its scale ascale[c Rp + row] and
+// the two FP16 terms of every entry.
+__global__ void k_split_operators_f16(int ncls, int R, int P, int Rp, int Kp, const double *__restrict__ op,
+                                      uint16_t *opt, float *ascale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nrow = (int64_t)ncls * R;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nrow;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int c = (int)(w / R), row = (int)(w % R);
+        const double *o = op + w * P;
+        double m = 0.0;
+        for (int k = lane; k < P; k += 32) m = fmax(m, fabs(o[k]));
+        for (int sft = 16; sft; sft >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, sft));
+        const int e = f16_exp(m);
+        const double inv = ldexp(1.0, -e);
+        for (int k = lane; k < P; k += 32) {
+            uint16_t t[2];
+            split_f16(o[k] * inv, t);
+            opt[((int64_t)c * Rp + row) * Kp + k] = t[0];
+            opt[(((int64_t)ncls + c) * Rp + row) * Kp + k] = t[1];
+        }
+        if (lane == 0) ascale[(int64_t)c * Rp + row] = ldexpf(1.f, e);
+    }
+}
+
+// Scale exponent of every cell's moment (scaled FP16 form): one CTA per cell.
+__global__ void k_cell_scale(int P, const double *__restrict__ M, int *cexp, StepWhen w)
+{
+    if (w.alpha && when_interval(w) < 0) return;
+    __shared__ double red[8];
+    const double *m = M + (int64_t)blockIdx.x * P;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) v = fmax(v, fabs(m[k]));
+    for (int sft = 16; sft; sft >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, sft));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = fmax(v, red[k]);
+        v = fmax(v, red[0]);
+        cexp[blockIdx.x] = f16_exp(v);
+    }
+}
+
+// Gather of the scaled FP16 form: Bt[k][col][r] = term k of M_S[g(b) +
+// P3 n] 2^-e_S, and bscale[col] = 2^e_S.
+__global__ void k_m2l_gather_f16(int64_t np, int P3, int P, int Kp, const int32_t *__restrict__ pS,
+                                 const uint8_t *__restrict__ pg, const int16_t *__restrict__ perm,
+                                 const double *__restrict__ M, const int *__restrict__ cexp, uint16_t *Bt,
+                                 float *bscale, StepWhen w)
+{
+    if (w.alpha && when_interval(w) < 0) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np * P; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = e / P;
+        const int r = (int)(e % P), b = r % P3;
+        const int S = pS[col], ex = cexp[S];
+        uint16_t t[2];
+        split_f16(ldexp(M[(int64_t)S * P + perm[pg[col] * P3 + b] + (r - b)], -ex), t);
+        Bt[col * Kp + r] = t[0];
+        Bt[(np + col) * Kp + r] = t[1];
+        if (r == 0) bscale[col] = ldexpf(1.f, ex);
     }
 }
 
@@ -1082,7 +1167,9 @@ static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V, StepWhen w = StepWhe
     for (int p = 0; p < F.nprod; ++p) g.prod[p] = F.prod[p];
     g.kchunks = F.Kp / kTcBK;
     g.nstage = tc_stages(F.nta, F.ntb, V.tile_n);
-    g.fmt = 1;
+    g.fmt = F.f16 ? 0 : 1;
+    g.a_scale = F.f16 ? V.ascale : nullptr;
+    g.b_scale = F.f16 ? V.bscale : nullptr;
     g.ldc = F.R;
     g.C = V.C32;
     g.tiles = V.tiles;
@@ -1285,8 +1372,11 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     } else {
         // tensor-core forms: BF16 terms of operators and moments, and the
         // products (A term, B term) kept: all with s + t < nterm
-        const int nterm = c->P.precision == 1 ? 3 : c->P.precision == 2 ? 2 : 1;
+        // (precision 4: two FP16 terms with power-of-two scales, products
+        // (0,0), (0,1), (1,0))
+        const int nterm = c->P.precision == 1 ? 3 : (c->P.precision == 2 || c->P.precision == 4) ? 2 : 1;
         F.nta = F.ntb = nterm;
+        F.f16 = c->P.precision == 4;
         F.nprod = 0;
         for (int sum = 0; sum < nterm; ++sum)
             for (int a = 0; a <= sum; ++a) F.prod[F.nprod++] = (a << 4) | (sum - a);
@@ -1367,6 +1457,8 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     }
     F_TRY(cudaMemcpyAsync(F.Tm, tm.data(), tm.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
     F_TRY(falloc(c, &F.far, (size_t)F.Lt * ns));
+    F_TRY(falloc(c, &F.Tq, (size_t)ns * pt));
+    F_TRY(falloc(c, &F.Tu, (size_t)ns * pt));
 
     for (int l = 2; l <= L; ++l) {
         FmmLevel &V = F.lev[l];
@@ -1518,7 +1610,15 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
             } else {
                 // BF16 terms of the operators; zero blocks; the FP64 stacks go
                 F_TRY(falloc(c, &V.opt, (size_t)F.nta * V.ncls * F.Rp * F.Kp));
-                k_split_operators<<<152 * 32, 256, 0, c->s>>>(V.ncls, F.R, P, F.Rp, F.Kp, F.nta, op, V.opt);
+                if (F.f16) {
+                    F_TRY(falloc(c, &V.ascale, (size_t)V.ncls * F.Rp));
+                    F_TRY(falloc(c, &V.bscale, (size_t)V.np));
+                    F_TRY(falloc(c, &V.cexp, (size_t)V.nc));
+                    k_split_operators_f16<<<152 * 32, 256, 0, c->s>>>(V.ncls, F.R, P, F.Rp, F.Kp, op, V.opt,
+                                                                      V.ascale);
+                } else {
+                    k_split_operators<<<152 * 32, 256, 0, c->s>>>(V.ncls, F.R, P, F.Rp, F.Kp, F.nta, op, V.opt);
+                }
                 F_TRY(cudaGetLastError());
                 double *d_bm = nullptr;
                 F_TRY(falloc(c, &d_bm, (size_t)V.ncls * F.ngb));
@@ -1567,9 +1667,14 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
         }
         return w;
     };
-    if (!graph) ++c->far_kernels;
-    k_p2m<<<TL.nc, 128, 0, s>>>(F.P3, P, F.Lt, k, d, c->ns, c->P.nt - 2, TL.cstart, c->tree.perm, F.At, F.As, c->d_q,
-                                c->d_u, F.wk, F.tl, pref, F.lev[L].M, when(1));
+    if (!graph) c->far_kernels += 2;
+    {
+        const int64_t nx = (int64_t)c->ns * F.pt;
+        k_p2m_time<<<(int)((nx + 255) / 256), 256, 0, s>>>(c->ns, F.pt, F.Lt, k, d, c->P.nt - 2, c->tree.perm, c->d_q,
+                                                           c->d_u, F.wk, F.tl, F.Tq, F.Tu, when(1));
+        k_p2m_moments<<<dim3(TL.nc, (P + 255) / 256), 256, 0, s>>>(F.P3, P, TL.cstart, c->tree.perm, F.At, F.As, F.Tq,
+                                                                   F.Tu, pref, F.lev[L].M, when(1));
+    }
     F_TRY(cudaGetLastError());
     size_t shm = 2 * P * sizeof(double);
     for (int l = L; l >= 2; --l) {
@@ -1588,7 +1693,11 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
             const int64_t n = V.np * P;
             const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
             if (!graph) c->far_kernels += 3;  // gather, products, reduction
-            if (c->split)
+            if (F.f16) {
+                k_cell_scale<<<V.nc, 256, 0, s>>>(P, V.M, V.cexp, w);
+                k_m2l_gather_f16<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, V.pS, V.pg, F.perm, V.M, V.cexp, V.Bt,
+                                                     V.bscale, w);
+            } else if (c->split)
                 k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt, w);
             else
                 k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf, w);

@@ -227,7 +227,7 @@ __device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_
 
 template <bool HU, bool HW, bool SPLIT, int WPR, bool COL>
 __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const int64_t *__restrict__ prow,
-                                         const int32_t *__restrict__ col, const int64_t *__restrict__ rowblk,
+                                         const int32_t *__restrict__ crow, const int64_t *__restrict__ rowblk,
                                          const uint16_t *__restrict__ meta, const int64_t *__restrict__ boff,
                                          const double *__restrict__ ku, const double *__restrict__ kw,
                                          const double *__restrict__ u_, const double *__restrict__ q,
@@ -249,7 +249,6 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
     const int64_t p0 = prow[i];
     const int npr = (int)(prow[i + 1] - p0);
     const uint16_t *mrow = meta + p0;
-    const int32_t *crow = COL ? col + p0 : nullptr;  // COL: explicit columns (near lists), else j = pair index
     const int64_t *orow = boff + rowblk[i];
     const int nblk = (int)(rowblk[i + 1] - rowblk[i]);
     const V *kuv = reinterpret_cast<const V *>(ku);
@@ -305,7 +304,11 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
 // b_i = -e_i - sum_j sum_{g in window(i,j), g <= a} (KU^(g)_ij q_j^{a-g} - KW^(g)_ij u_j^{a-g})
 // WPR warps per row i (4: the CTA's warps share the row's 32-pair blocks in
 // turn; 1: four rows per CTA); COL: the rows carry explicit columns (near
-// lists), else the column is the pair index (all pairs).  Every load of the
+// lists: the list of the row's leaf cell, col + coff[e2c[i]], shared by all
+// rows of the cell; rows taken in the octree's sorted order rowperm, so
+// that the rows of a cell run together and find the cell's columns and the
+// neighbours' histories in cache), else the column is the pair index (all
+// pairs).  Every load of the
 // coefficient stream is a contiguous warp access, and the history entries
 // x_j^{a-g} of one slot differ only by the lanes' g0.  The row sum is
 // reduced in a fixed order (deterministic).
@@ -316,6 +319,9 @@ template <bool HU, bool HW, bool SPLIT, int WPR, bool COL>
 __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
                                                               const int64_t *__restrict__ prow,
                                                               const int32_t *__restrict__ col,
+                                                              const int64_t *__restrict__ coff,
+                                                              const int32_t *__restrict__ e2c,
+                                                              const int32_t *__restrict__ rowperm,
                                                               const int64_t *__restrict__ rowblk,
                                                               const uint16_t *__restrict__ meta,
                                                               const int64_t *__restrict__ boff,
@@ -340,10 +346,15 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
     }
     // WPR warps per row, kNearWarps / WPR rows per CTA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (kNearWarps / WPR) + warp / WPR, wr = warp % WPR;
+    const int r = blockIdx.x * (kNearWarps / WPR) + warp / WPR, wr = warp % WPR;
+    const int i = (COL && r < ns) ? rowperm[r] : r;
     double acc = 0.0;
     DF dacc = {0.f, 0.f};
-    if (i < ns) near_row<HU, HW, SPLIT, WPR, COL>(i, wr, ns, alpha, prow, col, rowblk, meta, boff, ku, kw, u_, q, us, qs, dacc, acc);
+    if (i < ns) {
+        const int32_t *crow = COL ? col + coff[e2c[i]] : nullptr;
+        near_row<HU, HW, SPLIT, WPR, COL>(i, wr, ns, alpha, prow, crow, rowblk, meta, boff, ku, kw, u_, q, us, qs,
+                                          dacc, acc);
+    }
     if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
@@ -372,8 +383,10 @@ static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, c
     constexpr int rows = kNearWarps / WPR;
     // the kernel uses a pair's column only to address the history: in the
     // split form with near lists that is the column's sorted position
-    const int32_t *hcol = (SPLIT && c->d_hcol) ? c->d_hcol : c->d_col;
-    k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, hcol, c->d_rowblk, c->d_meta, c->d_boff,
+    const int32_t *hcol = COL ? ((SPLIT && c->d_chcol) ? c->d_chcol : c->d_ccol) : nullptr;
+    k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, hcol,
+                                       COL ? c->d_coff : nullptr, COL ? c->tree.e2c : nullptr,
+                                       COL ? c->tree.perm : nullptr, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
                                        c->d_n, d_far, c->alpha_dev_on && d_far ? c->fmm.Lt : 0, c->P.nt - 1, c->d_b);
     return cudaGetLastError();

@@ -276,14 +276,23 @@ __global__ void __launch_bounds__(192, 1)
             }
             const TcTile t = g.tiles[tile];
             float *out = g.C + t.c_off + row;
+            const float sa = (g.a_scale && row < t.rows) ? g.a_scale[t.a_row + row] : 1.f;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c0), r);
                 if (row < t.rows) {
+                    if (g.a_scale) {
 #pragma unroll
-                    for (int x = 0; x < 32; ++x)
-                        if (c0 + x < t.cols) out[(int64_t)(c0 + x) * g.ldc] = __uint_as_float(r[x]);
+                        for (int x = 0; x < 32; ++x)
+                            if (c0 + x < t.cols)
+                                out[(int64_t)(c0 + x) * g.ldc] =
+                                    __uint_as_float(r[x]) * sa * g.b_scale[t.b_row + c0 + x];
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < 32; ++x)
+                            if (c0 + x < t.cols) out[(int64_t)(c0 + x) * g.ldc] = __uint_as_float(r[x]);
+                    }
                 }
             }
             tc_fence_before();

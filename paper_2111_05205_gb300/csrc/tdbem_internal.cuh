@@ -136,6 +136,8 @@ struct TcGemmArgs {
     int32_t ntiles;
     int *err;                         // bit 3 (value 8) is set when a pipeline wait gave up
     StepWhen when;                    // graph-replayed steps: run only at the level's M2L steps
+    const float *a_scale;             // per A row (term-0 row index) and per B row: the result is
+    const float *b_scale;             // multiplied by both in the epilogue (nullptr: no scaling)
 };
 
 cudaError_t tc_make_map(CUtensorMap *map, const void *base, int64_t rows, int kp, int box_rows);
@@ -191,6 +193,9 @@ struct FmmLevel {
     // tensor-core forms: split terms of operators and moments, FP32 products
     uint16_t *opt = nullptr;     // [nta][ncls][Rp][Kp] BF16 operator terms
     uint16_t *Bt = nullptr;      // [ntb][np][Kp] BF16 moment terms
+    float *ascale = nullptr;     // scaled FP16 form: [ncls][Rp] row scales of the operator terms
+    float *bscale = nullptr;     // scaled FP16 form: [np] column scales of the moment terms
+    int *cexp = nullptr;         // scaled FP16 form: [nc] scale exponent of each cell's moment
     float *C32 = nullptr;        // [np][mu P] products
     TcTile *tiles = nullptr;     // [ntiles] GEMM tiles (zero operator blocks skipped)
     int ntiles = 0;
@@ -208,6 +213,7 @@ struct Fmm {
     int ngb = 0;                            // operator blocks applied as GEMMs (near future 1..mu)
     int R = 0, Rp = 0, Kp = 0;              // their rows ngb P, rows padded to 128, K padded to 64
     int nta = 0, ntb = 0, nprod = 0;        // tensor-core forms: split terms and products
+    bool f16 = false;                       // precision 4: two FP16 terms with power-of-two scales
     int prod[kTcMaxProd] = {0};
     int16_t *perm = nullptr;                // [48][P3] node permutation of each symmetry element
     int16_t *iperm = nullptr;               // [48][P3] its inverse
@@ -219,6 +225,7 @@ struct Fmm {
     double *Tm = nullptr;                   // [2][pt][pt] time transfer
     double *wt = nullptr;                   // [pt] Chebyshev time nodes
     double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
+    double *Tq = nullptr, *Tu = nullptr;    // [ns][pt] P2M time sums of the folded histories (sorted order)
     int far_k = -1;                         // leaf interval the far field belongs to
 };
 
@@ -288,6 +295,10 @@ struct tdbem_ctx {
     // history gathers are contiguous runs; d_hpos[i] = position of element i,
     // d_hcol = the near pairs' columns as positions (nullptr otherwise)
     int32_t *d_hpos = nullptr, *d_hcol = nullptr;
+    // near lists per leaf cell (every element of a cell has the same list):
+    // element numbers d_ccol, sorted positions d_chcol, cell c from d_coff[c]
+    int64_t *d_coff = nullptr;
+    int32_t *d_ccol = nullptr, *d_chcol = nullptr;
     double *d_b = nullptr, *d_xa = nullptr, *d_xb = nullptr;
     int ell_w = 0;               // off-diagonal entries per row of the zero-lag store
     int jac_grid = 0;            // CTAs of the fused Jacobi launch (0: one launch per sweep)

@@ -340,6 +340,40 @@ __global__ void k_near_fill(int ns, const int32_t *__restrict__ e2c, const int32
     }
 }
 
+// The near list is the same for every element of a leaf cell: per cell c,
+// the elements of its neighbour cells (key order, sorted order within a
+// cell) as element numbers ccol and as sorted positions chcol, from
+// coff[c].  (The per-step history sum reads these instead of per-pair
+// columns.)
+__global__ void k_cell_near_count(int nc, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncount,
+                                  const int32_t *__restrict__ cstart, int64_t *cnt)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int64_t n = 0;
+    for (int a = 0; a < ncount[c]; ++a) {
+        int m = nbr[(int64_t)c * 27 + a];
+        n += cstart[m + 1] - cstart[m];
+    }
+    cnt[c] = n;
+}
+
+__global__ void k_cell_near_fill(int nc, const int32_t *__restrict__ nbr, const int32_t *__restrict__ ncount,
+                                 const int32_t *__restrict__ cstart, const int32_t *__restrict__ perm,
+                                 const int64_t *__restrict__ coff, int32_t *ccol, int32_t *chcol)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int64_t o = coff[c];
+    for (int a = 0; a < ncount[c]; ++a) {
+        int m = nbr[(int64_t)c * 27 + a];
+        for (int p = cstart[m]; p < cstart[m + 1]; ++p) {
+            chcol[o] = p;
+            ccol[o++] = perm[p];
+        }
+    }
+}
+
 __global__ void k_invert_perm(int ns, const int32_t *__restrict__ perm, int32_t *pos)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -397,6 +431,35 @@ cudaError_t build_near_lists(tdbem_ctx *c)
     k_near_fill<<<(ns + 127) / 128, 128, 0, s>>>(ns, e2c, T.nbr, T.ncount, T.cstart, c->tree.perm, c->d_prow,
                                                 c->d_col, c->d_hcol);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // per-cell near lists for the history sum
+    {
+        const int nc = T.nc;
+        int64_t *ccnt = nullptr;
+        if ((e = cudaMalloc(&ccnt, nc * sizeof(int64_t))) != cudaSuccess) return e;
+        k_cell_near_count<<<(nc + 127) / 128, 128, 0, s>>>(nc, T.nbr, T.ncount, T.cstart, ccnt);
+        std::vector<int64_t> hcc(nc), coff(nc + 1, 0);
+        if ((e = cudaMemcpyAsync(hcc.data(), ccnt, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        cudaFree(ccnt);
+        for (int k = 0; k < nc; ++k) coff[k + 1] = coff[k] + hcc[k];
+        void *q1, *q2, *q3;
+        if ((e = cudaMalloc(&q1, (nc + 1) * sizeof(int64_t))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&q2, std::max<int64_t>(coff[nc], 1) * sizeof(int32_t))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&q3, std::max<int64_t>(coff[nc], 1) * sizeof(int32_t))) != cudaSuccess) return e;
+        c->allocs.push_back(q1);
+        c->allocs.push_back(q2);
+        c->allocs.push_back(q3);
+        c->d_coff = (int64_t *)q1;
+        c->d_ccol = (int32_t *)q2;
+        c->d_chcol = (int32_t *)q3;
+        if ((e = cudaMemcpyAsync(c->d_coff, coff.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return e;
+        k_cell_near_fill<<<(nc + 127) / 128, 128, 0, s>>>(nc, T.nbr, T.ncount, T.cstart, c->tree.perm, c->d_coff,
+                                                         c->d_ccol, c->d_chcol);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return cudaStreamSynchronize(s);
 }
 
