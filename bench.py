@@ -9,10 +9,11 @@ The workload is the seeded synthetic scattering problem with Ns = 20480: a
 sound-hard ellipsoid (icosphere subdivision 5 mapped by axes ~ U[0.5, 1.5],
 seed 3), Burton-Miller BIE, B-spline order d = 2, c dt = 0.5 x mean edge,
 Gaussian plane pulse (sigma = 0.3, seeded direction), Nt = 1024.  The FMM
-runs at octree depth 3 with ps = pt = 8 interpolation points by default (the
-fastest configuration measured whose whole march stays within 1e-3 of the
-direct path); the configuration table's depth 5 with orders 5/5 and depth 4
-with 6/6 are measured beside it.
+runs at octree depth 3 with ps = 7, pt = 8 interpolation points and the M2L
+in two scaled FP16 terms by default (the fastest configuration measured
+whose whole march stays within 1e-3 of the direct path); the configuration
+table's depth 5 with orders 5/5, depth 4 with 6/6 and depth 3 with 8/8 are
+measured beside it.
 
 The timed steps are whole cycles of the FMM's interval pattern (the leaf
 interval times 2^(depth-2) steps, so that every level's M2L occurs in its
@@ -256,7 +257,7 @@ def run_fmm(args):
     out = {
         "metric": METRIC, "value": world * 1000.0 / ms_step, "unit": "time-steps/s", "n_gpus": world,
         "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16" if prec else "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": ("f64+f16" if prec == 4 else "f64+bf16") if prec else "f64", "data": "synthetic",
         "e2e": {"value": world * e2e, "unit": "time-steps/s", "h2d_bytes_per_step": w.ns * 8,
                 "d2h_bytes_per_step": w.ns * 8},
         "clocks": clk.summary(),
@@ -276,9 +277,10 @@ def run_fmm(args):
         tc = st["gemm_tc_flops"] / (st["ms_gemm"] * 1e-3) / 1e12 if st["ms_gemm"] > 0 else 0.0
         gemm_obj = {
             "bound": "tensor", "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16,
-            "traffic": None, "kernel": "k_tc_gemm (M2L, tcgen05)", "peak_source": bf_kind + " bf16 burst",
+            "traffic": None, "kernel": "k_tc_gemm (M2L, tcgen05)",
+            "peak_source": bf_kind + " bf16 burst" + (" (FP16 has the same nominal dense rate)" if prec == 4 else ""),
             "flops_per_launch": st["gemm_tc_flops"] / max(st["launches_gemm"], 1), "avg_launch_ms": gemm_ms,
-            "flops": "BF16 tensor-pipe flops the split needs: %d products x 2 P per kept operator row and pair "
+            "flops": "16-bit tensor-pipe flops the split needs: %d products x 2 P per kept operator row and pair "
                      "(K and tile padding not counted)" % nprod,
             "useful_tflops": tc / nprod, "useful_frac": tc / nprod / bf16}
     else:
@@ -348,7 +350,7 @@ def run_fmm(args):
             # other hierarchies of the same problem: the configuration
             # table's depth 5 with orders 5/5, and depth 4 with 6/6
             out["other_forms"] = []
-            for depth, ps, pt in ((5, 5, 5), (4, 6, 6)):
+            for depth, ps, pt in ((5, 5, 5), (4, 6, 6), (3, 8, 8)):
                 if (depth, ps, pt) == (args.depth, args.ps, args.pt):
                     continue
                 v = _solver(w, phi, stream, prec, (ps, pt, 0), depth)
@@ -994,13 +996,13 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="split", choices=["split", "fp64", "bf16x3", "bf16", "f16x2"])
+    ap.add_argument("--precision", default="f16x2", choices=["split", "fp64", "bf16x3", "bf16", "f16x2"])
     ap.add_argument("--fp64-steps", type=int, default=240,
                     help="--algo fmm: steps the FP64 form is marched for its comparison")
     ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false")
     ap.add_argument("--algo", default="fmm", choices=["direct", "fmm"])
     ap.add_argument("--depth", type=int, default=3)
-    ap.add_argument("--ps", type=int, default=8)
+    ap.add_argument("--ps", type=int, default=7)
     ap.add_argument("--pt", type=int, default=8)
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="--algo fmm: skip the other (depth, orders) forms measured beside the headline")

@@ -287,7 +287,8 @@ int tdbem_sai_gradient(tdbem_sai *sai, tdbem_ctx *ctx, float *grad, float *loss)
  * floats) to inout, set = 1 loads inout (and resets the optimiser). */
 int tdbem_sai_weights(tdbem_sai *sai, float *inout, int64_t *count, int32_t set);
 /* Installs the network's M as the context's zero-lag solver (sweeps
- * x <- x + M (b - A x), all K of a step in one cooperative launch with a
+ * x <- x + M (b - A x), run as x_0 = M b, x <- M b + (I - M A) x with I - M A
+ * formed once at installation; all K of a step in one cooperative launch with a
  * bounded grid barrier where the device supports it, else one launch each;
  * K from ||I - M A||_inf so that the error stays below solver_tol) when that
  * takes fewer sweeps than Jacobi; otherwise Jacobi stays.  *use_sai,

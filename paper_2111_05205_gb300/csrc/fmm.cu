@@ -676,6 +676,56 @@ __global__ void k_m2l_reduce(int nc, int P3, int P, int nblk, int mu, int nslot,
     }
 }
 
+// The same reduction with coalesced reads (tensor-core forms): one CTA per
+// (observation cell, chunk of rows [r0, r0 + nrow), a multiple of P3); for
+// each pair in list order the CTA reads the chunk of the pair's product
+// contiguously and adds row a_c + rest to the double-float accumulator of
+// row perm_g(a_c) + rest in shared memory (the same additions in the same
+// order as k_m2l_reduce, so the same bits); a barrier between pairs.
+__global__ void k_m2l_reduce_smem(int nc, int P3, int P, int nblk, int mu, int nslot, int k, int nrow,
+                                  const int64_t *__restrict__ ooff, const int64_t *__restrict__ oidx,
+                                  const uint8_t *__restrict__ og, const int16_t *__restrict__ perm,
+                                  const float *__restrict__ C, double *ring, StepWhen w)
+{
+    if (w.alpha && (k = when_interval(w)) < 0) return;
+    extern __shared__ float acc[];  // [nrow] hi, [nrow] lo
+    float *hi = acc, *lo = acc + nrow;
+    const int R = nblk * P;
+    const int O = blockIdx.x;
+    const int r0 = blockIdx.y * nrow;
+    const int n = min(nrow, R - r0);
+    const int64_t t0 = ooff[O];
+    const int nt = (int)(ooff[O + 1] - t0);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) hi[e] = lo[e] = 0.f;
+    for (int t = 0; t < nt; ++t) {
+        __syncthreads();
+        const float *col = C + oidx[t0 + t] * R + r0;
+        const int16_t *pg = perm + og[t0 + t] * P3;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int a = (r0 + e) % P3;
+            const int d = e - a + pg[a];
+            float h = hi[d], l = lo[d];
+            two_sum_acc(h, l, col[e]);
+            hi[d] = h;
+            lo[d] = l;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int row = r0 + e;
+        const int blk = row / P, r = row % P;
+        ring[((int64_t)((k + blk + 1) % nslot) * nc + O) * P + r] += (double)hi[e] + (double)lo[e];
+    }
+}
+
+// Rows per CTA of k_m2l_reduce_smem: the largest multiple of P3 whose two
+// float accumulators fit in shared memory.
+static int reduce_rows(int P3, int R)
+{
+    const int per = (kTcSmemBudget / (2 * (int)sizeof(float))) / P3 * P3;
+    return std::min(per, R);
+}
+
 // Distance powers between the nodes of a canonical offset's observation and
 // source boxes: kr[c][e][a][b] = r_ab^(e-1) (e = 0: 1/r), e = 0..d (the
 // slot e = 1, r^0 = 1, is not read), r_ab = |-c s + ho w_a - hs w_b|.
@@ -850,9 +900,32 @@ __global__ void k_deriv_moments(int64_t np, int P3, int pt, const int32_t *__res
 //   Fp[col][e][j][a] = sum_b r_ab^(e-1) mu[col][j][b]  (e != 1, e + j <= D - 1),
 // a in the canonical node order (D = d + 1).  One CTA per (class, 8
 // columns), one thread per row a; the matrices go through shared memory cw
-// (32, or 16 for the largest boxes) columns at a time (rows padded to cw + 1
-// entries), so each chunk serves 8 columns.
+// columns at a time (rows padded to cw + 1 entries), so each chunk serves 8
+// columns, in two buffers: the next chunk is copied (cp.async, 8 bytes per
+// entry) while the current one is used.
 constexpr int kDerivCols = 8;
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void deriv_chunk_load(const T *__restrict__ K, int P3, int cw, int b0, T *buf)
+{
+    for (int x = threadIdx.x; x < P3 * cw; x += blockDim.x) {
+        const int row = x / cw, cc = x % cw;
+        T *dst = buf + row * (cw + 1) + cc;
+        if (b0 + cc < P3)
+            cp_async8(dst, K + (int64_t)row * P3 + b0 + cc);
+        else
+            *dst = gen_from<T>(0.0);
+    }
+}
 
 template <typename T, int D>
 __global__ void __launch_bounds__(512) k_deriv_products(int P3, int cw, const int4 *__restrict__ jobs, const T *__restrict__ kr,
@@ -861,7 +934,7 @@ __global__ void __launch_bounds__(512) k_deriv_products(int P3, int cw, const in
     if (w.alpha && when_interval(w) < 0) return;
     extern __shared__ double shm_d[];
     T *mus = reinterpret_cast<T *>(shm_d);    // [kDerivCols][D][P3]
-    T *kc = mus + kDerivCols * D * P3;        // [P3][cw + 1]
+    T *kc[2] = {mus + kDerivCols * D * P3, mus + kDerivCols * D * P3 + P3 * (cw + 1)};  // [P3][cw + 1] each
     const int4 job = jobs[blockIdx.x];        // class, first column, columns
     const int cls = job.x, ncol = job.z;
     const int64_t col0 = job.y;
@@ -870,6 +943,7 @@ __global__ void __launch_bounds__(512) k_deriv_products(int P3, int cw, const in
         const int t = x / (D * P3);
         mus[x] = t < ncol ? mu[col0 * D * P3 + x] : gen_from<T>(0.0);
     }
+    const int nch = (P3 + cw - 1) / cw;
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         if (e == 1) continue;
@@ -879,23 +953,31 @@ __global__ void __launch_bounds__(512) k_deriv_products(int P3, int cw, const in
 #pragma unroll
             for (int j = 0; j < D; ++j) acc[t][j] = gen_from<T>(0.0);
         const T *K = kr + ((int64_t)cls * D + e) * P3 * P3;
-        for (int b0 = 0; b0 < P3; b0 += cw) {
-            __syncthreads();
-            for (int x = threadIdx.x; x < P3 * cw; x += blockDim.x) {
-                const int row = x / cw, cc = x % cw;
-                kc[row * (cw + 1) + cc] = (b0 + cc < P3) ? K[(int64_t)row * P3 + b0 + cc] : gen_from<T>(0.0);
+        __syncthreads();  // both buffers free (previous e done)
+        deriv_chunk_load(K, P3, cw, 0, kc[0]);
+        cp_async_commit();
+        for (int ci = 0; ci < nch; ++ci) {
+            const int b0 = ci * cw;
+            if (ci + 1 < nch) {
+                deriv_chunk_load(K, P3, cw, b0 + cw, kc[(ci + 1) & 1]);
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
             if (r < P3) {
+                const T *kb = kc[ci & 1];
                 const int nb = min(cw, P3 - b0);
                 for (int cc = 0; cc < nb; ++cc) {
-                    const T x = kc[r * (cw + 1) + cc];
+                    const T x = kb[r * (cw + 1) + cc];
 #pragma unroll
                     for (int t = 0; t < kDerivCols; ++t)
 #pragma unroll
                         for (int j = 0; j + e < D; ++j) gen_fma(acc[t][j], x, mus[(t * D + j) * P3 + b0 + cc]);
                 }
             }
+            __syncthreads();  // kc[ci & 1] is refilled by the next iteration's copy
         }
         if (r < P3)
 #pragma unroll
@@ -968,15 +1050,16 @@ __global__ void k_deriv_assemble(int nc, int P3, int pt, int nslot, int k, int m
     }
 }
 
-// Shared memory of the products kernel and its chunk width (32 columns of
-// the distance-power matrices, 16 where 32 do not fit).
+// Shared memory of the products kernel (the columns' moments and two
+// chunk buffers) and its chunk width: 32 columns of the distance-power
+// matrices, else 16 or 8, whichever fits first.
 static size_t deriv_shm(int D, int P3, size_t el, int *cw)
 {
-    *cw = 32;
-    size_t b = ((size_t)kDerivCols * D * P3 + (size_t)P3 * 33) * el;
-    if (b > (size_t)kTcSmemBudget) {
-        *cw = 16;
-        b = ((size_t)kDerivCols * D * P3 + (size_t)P3 * 17) * el;
+    size_t b = 0;
+    for (int w : {32, 16, 8}) {
+        *cw = w;
+        b = ((size_t)kDerivCols * D * P3 + 2 * (size_t)P3 * (w + 1)) * el;
+        if (b <= (size_t)kTcSmemBudget) break;
     }
     return b;
 }
@@ -1712,10 +1795,14 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
                 c->launches[PH_GEMM] += c->split ? 1 : V.ncls;
                 c->gemm_tc_flops += V.flops_app * (c->split ? F.nprod : 1);
             }
-            if (c->split)
-                k_m2l_reduce<float><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx, V.og,
-                                                         F.iperm, V.C32, V.ring, V.G, w);
-            else
+            if (c->split) {
+                const int nrow = reduce_rows(F.P3, F.R);
+                const size_t shm = 2 * sizeof(float) * (size_t)nrow;
+                if (shm > 48 * 1024)
+                    F_TRY(cudaFuncSetAttribute(k_m2l_reduce_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+                k_m2l_reduce_smem<<<dim3(V.nc, (F.R + nrow - 1) / nrow), 512, shm, s>>>(
+                    V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, nrow, V.ooff, V.oidx, V.og, F.perm, V.C32, V.ring, w);
+            } else
                 k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx,
                                                           V.og, F.iperm, V.Cbuf, V.ring, V.G, w);
             F_TRY(cudaGetLastError());

@@ -458,7 +458,24 @@ __device__ __forceinline__ double jacobi_row(int i, int ns, int width, const dou
 {
     double s = b[i];
     if (xin) {
-        for (int k = 0; k < width; ++k) {
+        // four entries at a time: their columns and values first, then the
+        // four gathers of x, so that the loads of a group are in flight together
+        int k = 0;
+        for (; k + 4 <= width; k += 4) {
+            int cidx[4];
+            double a[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                cidx[u] = acol[(int64_t)(k + u) * ns + i];
+                a[u] = aoff[(int64_t)(k + u) * ns + i];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = cidx[u] >= 0 ? ldx(xin + cidx[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cidx[u] >= 0) s -= a[u] * xv[u];
+        }
+        for (; k < width; ++k) {
             int cidx = acol[(int64_t)k * ns + i];
             if (cidx >= 0) s -= aoff[(int64_t)k * ns + i] * ldx(xin + cidx);
         }

@@ -251,33 +251,51 @@ __global__ void k_sai_apply_net(int ns, int ell_w, int W, int H, const double *_
     }
 }
 
-// Row i of one preconditioned sweep x' = x + M (b - A x) (x == nullptr:
-// x' = M b), the residual of each row j of M's pattern recomputed on the fly.
-// Shared by the one-sweep and the fused kernels, so both give the same bits.
-template <typename LDX>
-__device__ __forceinline__ double sai_row_sweep(int i, int ns, int W, int ell_w, const double *__restrict__ mval,
-                                                const int32_t *__restrict__ mcol, const double *__restrict__ aoff,
-                                                const int32_t *__restrict__ acol, const double *__restrict__ ainv,
-                                                const double *__restrict__ b, const double *x, LDX ldx)
+// The preconditioned sweeps x_{k+1} = x_k + M (b - A x_k), x_0 = M b, are
+// run as x_0 = c = M b, x_{k+1} = c + G x_k with G = I - M A formed once
+// when the SAI is installed (ELL store [gw][ns]): one gather per entry of G
+// instead of recomputing rows of A x for every entry of M.
+__device__ __forceinline__ double sai_mb(int i, int ns, int W, const double *__restrict__ mval,
+                                         const int32_t *__restrict__ mcol, const double *__restrict__ b)
 {
-    double s = x ? ldx(x + i) : 0.0;
+    double s = 0.0;
     for (int k = 0; k < W; ++k) {
-        int j = mcol[(int64_t)k * ns + i];
-        if (j < 0) continue;
-        double r = b[j];
-        if (x) {
-            r -= ldx(x + j) / ainv[j];
-            for (int e = 0; e < ell_w; ++e) {
-                int l = acol[(int64_t)e * ns + j];
-                if (l >= 0) r -= aoff[(int64_t)e * ns + j] * ldx(x + l);
-            }
-        }
-        s += mval[(int64_t)k * ns + i] * r;
+        const int j = mcol[(int64_t)k * ns + i];
+        if (j >= 0) s += mval[(int64_t)k * ns + i] * b[j];
     }
     return s;
 }
 
-// The last sweep adds x' to the unknown component of step a-1 and flags a
+template <typename LDX>
+__device__ __forceinline__ double sai_g_row(int i, int ns, int gw, const double *__restrict__ gval,
+                                            const int32_t *__restrict__ gcol, const double *__restrict__ cb,
+                                            const double *x, LDX ldx)
+{
+    double s = cb[i];
+    // four entries at a time (columns and values, then the gathers of x)
+    int k = 0;
+    for (; k + 4 <= gw; k += 4) {
+        int l[4];
+        double g[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            l[u] = gcol[(int64_t)(k + u) * ns + i];
+            g[u] = gval[(int64_t)(k + u) * ns + i];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = l[u] >= 0 ? ldx(x + l[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (l[u] >= 0) s += g[u] * xv[u];
+    }
+    for (; k < gw; ++k) {
+        const int l = gcol[(int64_t)k * ns + i];
+        if (l >= 0) s += gval[(int64_t)k * ns + i] * ldx(x + l);
+    }
+    return s;
+}
+
+// The last sweep adds x_K to the unknown component of step a-1 and flags a
 // non-finite value (flag bit 1).
 __device__ __forceinline__ void sai_store(int i, double s, int64_t row, const int8_t *__restrict__ phi, double *u,
                                           double *q, float2 *us, float2 *qs, const int32_t *__restrict__ hpos,
@@ -293,18 +311,23 @@ __device__ __forceinline__ void sai_store(int i, double s, int64_t row, const in
     if (!isfinite(s)) atomicOr(flag, 1);
 }
 
-// One preconditioned sweep per launch.
-__global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__ mval, const int32_t *__restrict__ mcol,
-                            const double *__restrict__ aoff, const int32_t *__restrict__ acol,
-                            const double *__restrict__ ainv, const double *__restrict__ b,
-                            const double *__restrict__ x, double *xout, int last, int64_t row,
-                            const int8_t *__restrict__ phi, double *u, double *q, float2 *us, float2 *qs,
-                            const int32_t *__restrict__ hpos, int *flag)
+// One sweep per launch: it = 0 forms c = M b (x_0 = c); it > 0 one step of
+// x = c + G x; the last sweep stores.
+__global__ void k_sai_sweep(int ns, int W, int gw, const double *__restrict__ mval, const int32_t *__restrict__ mcol,
+                            const double *__restrict__ gval, const int32_t *__restrict__ gcol,
+                            const double *__restrict__ b, double *cb, const double *__restrict__ x, double *xout,
+                            int first, int last, int64_t row, const int8_t *__restrict__ phi, double *u, double *q,
+                            float2 *us, float2 *qs, const int32_t *__restrict__ hpos, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
-    const double s = sai_row_sweep(i, ns, W, ell_w, mval, mcol, aoff, acol, ainv, b, x,
-                                   [](const double *p) { return *p; });
+    double s;
+    if (first) {
+        s = sai_mb(i, ns, W, mval, mcol, b);
+        cb[i] = s;
+    } else {
+        s = sai_g_row(i, ns, gw, gval, gcol, cb, x, [](const double *p) { return *p; });
+    }
     if (last)
         sai_store(i, s, row, phi, u, q, us, qs, hpos, flag);
     else
@@ -313,22 +336,26 @@ __global__ void k_sai_sweep(int ns, int W, int ell_w, const double *__restrict__
 
 // All K sweeps of one step in one cooperative launch (rows grid-strided),
 // a bounded grid barrier between sweeps (x read with ld.global.cg, as in
-// the fused Jacobi solve).
-__global__ void __launch_bounds__(256) k_sai_fused(int ns, int W, int ell_w, const double *__restrict__ mval,
-                                                   const int32_t *__restrict__ mcol, const double *__restrict__ aoff,
-                                                   const int32_t *__restrict__ acol,
-                                                   const double *__restrict__ ainv, const double *__restrict__ b,
-                                                   double *xa, double *xb, int K, int64_t row,
+// the fused Jacobi solve); the same arithmetic as K launches of k_sai_sweep.
+__global__ void __launch_bounds__(256) k_sai_fused(int ns, int W, int gw, const double *__restrict__ mval,
+                                                   const int32_t *__restrict__ mcol, const double *__restrict__ gval,
+                                                   const int32_t *__restrict__ gcol, const double *__restrict__ b,
+                                                   double *cb, double *xa, double *xb, int K, int64_t row,
                                                    const int8_t *__restrict__ phi, double *u, double *q, float2 *us,
                                                    float2 *qs, const int32_t *__restrict__ hpos, int *flag,
                                                    unsigned *bar)
 {
     for (int it = 0; it < K; ++it) {
-        const double *xin = (it == 0) ? nullptr : ((it & 1) ? xa : xb);
+        const double *xin = (it & 1) ? xa : xb;
         double *xout = (it & 1) ? xb : xa;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
-            const double s = sai_row_sweep(i, ns, W, ell_w, mval, mcol, aoff, acol, ainv, b, xin,
-                                           [](const double *p) { return __ldcg(p); });
+            double s;
+            if (it == 0) {
+                s = sai_mb(i, ns, W, mval, mcol, b);
+                cb[i] = s;
+            } else {
+                s = sai_g_row(i, ns, gw, gval, gcol, cb, xin, [](const double *p) { return __ldcg(p); });
+            }
             if (it == K - 1)
                 sai_store(i, s, row, phi, u, q, us, qs, hpos, flag);
             else
@@ -529,9 +556,10 @@ int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_
     cudaMemcpyAsync(ac.data(), c->d_acol, ac.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->s);
     cudaMemcpyAsync(ai.data(), c->d_ainv, ai.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return TDBEM_ERR_CUDA;
-    // q' = max_i sum_l |delta_il - (M A)_il|
+    // q' = max_i sum_l |delta_il - (M A)_il|, and the rows of G = I - M A
     double qmax = 0.0;
     std::vector<std::pair<int, double>> acc;
+    std::vector<std::vector<std::pair<int, double>>> grows(ns);
     for (int i = 0; i < ns; ++i) {
         acc.clear();
         auto add = [&](int l, double v) {
@@ -556,12 +584,40 @@ int tdbem_set_precond(tdbem_ctx *c, const tdbem_sai *S, int32_t *use_sai, int32_
         double s = 0.0;
         for (auto &p : acc) s += fabs(p.second);
         qmax = std::max(qmax, s);
+        for (auto &p : acc)
+            if (p.second != 0.0) grows[i].push_back({p.first, -p.second});
     }
     double tol = c->P.solver_tol > 0 ? c->P.solver_tol : 1e-16;
     int K = (qmax > 0.0 && qmax < 1.0) ? std::max(1, (int)ceil(log(tol) / log(qmax))) : 1 << 30;
     // one launch per sweep for either solver
     bool better = qmax < 1.0 && K < c->solve_iters;
     if (better) {
+        // G in an ELL store [gw][ns] (unused slots: column -1)
+        size_t gw = 1;
+        for (auto &r : grows) gw = std::max(gw, r.size());
+        std::vector<double> gv(gw * ns, 0.0);
+        std::vector<int32_t> gc(gw * ns, -1);
+        for (int i = 0; i < ns; ++i)
+            for (size_t k = 0; k < grows[i].size(); ++k) {
+                gc[k * ns + i] = grows[i][k].first;
+                gv[k * ns + i] = grows[i][k].second;
+            }
+        double *gval = nullptr, *cb = nullptr;
+        int32_t *gcol = nullptr;
+        if (cudaMalloc(&gval, gv.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&gcol, gc.size() * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&cb, (size_t)ns * sizeof(double)) != cudaSuccess)
+            return TDBEM_ERR_OOM;
+        c->allocs.push_back(gval);
+        c->allocs.push_back(gcol);
+        c->allocs.push_back(cb);
+        if (cudaMemcpy(gval, gv.data(), gv.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(gcol, gc.data(), gc.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            return TDBEM_ERR_CUDA;
+        c->sai_gval = gval;
+        c->sai_gcol = gcol;
+        c->sai_gw = (int)gw;
+        c->sai_cb = cb;
         c->sai_val = mval;
         c->sai_col = mcol;
         c->sai_w = W;
@@ -590,9 +646,9 @@ namespace tdbem {
 // cooperative launch.
 cudaError_t launch_sai_fused(tdbem_ctx *c, int alpha)
 {
-    int ns = c->ns, W = c->sai_w, E = c->ell_w, K = c->sai_iters;
+    int ns = c->ns, W = c->sai_w, gw = c->sai_gw, K = c->sai_iters;
     int64_t row = (int64_t)(alpha - 1) * ns;
-    void *args[] = {&ns, &W, &E, &c->sai_val, &c->sai_col, &c->d_aoff, &c->d_acol, &c->d_ainv, &c->d_b,
+    void *args[] = {&ns, &W, &gw, &c->sai_val, &c->sai_col, &c->sai_gval, &c->sai_gcol, &c->d_b, &c->sai_cb,
                     &c->d_xa, &c->d_xb, &K, &row, &c->d_phi, &c->d_u, &c->d_q, &c->d_us, &c->d_qs, &c->d_hpos,
                     &c->d_flag, &c->d_bar};
     return cudaLaunchCooperativeKernel((const void *)k_sai_fused, dim3(c->sai_grid), dim3(256), args, 0, c->s);
@@ -603,12 +659,13 @@ cudaError_t launch_sai_sweep(tdbem_ctx *c, int alpha, int it)
 {
     const int ns = c->ns;
     const bool last = (it == c->sai_iters - 1);
-    const double *xin = (it == 0) ? nullptr : ((it & 1) ? c->d_xa : c->d_xb);
+    const double *xin = (it & 1) ? c->d_xa : c->d_xb;
     double *xout = (it & 1) ? c->d_xb : c->d_xa;
     int64_t row = (int64_t)(alpha - 1) * ns;
-    k_sai_sweep<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->sai_w, c->ell_w, c->sai_val, c->sai_col, c->d_aoff,
-                                                    c->d_acol, c->d_ainv, c->d_b, xin, xout, last, row, c->d_phi,
-                                                    c->d_u, c->d_q, c->d_us, c->d_qs, c->d_hpos, c->d_flag);
+    k_sai_sweep<<<(ns + 127) / 128, 128, 0, c->s>>>(ns, c->sai_w, c->sai_gw, c->sai_val, c->sai_col, c->sai_gval,
+                                                    c->sai_gcol, c->d_b, c->sai_cb, xin, xout, it == 0, last, row,
+                                                    c->d_phi, c->d_u, c->d_q, c->d_us, c->d_qs, c->d_hpos,
+                                                    c->d_flag);
     return cudaGetLastError();
 }
 

@@ -318,6 +318,10 @@ struct tdbem_ctx {
     int32_t *sai_col = nullptr;  // [sai_w][ns]
     int sai_w = 0, sai_iters = 0;
     int sai_grid = 0;            // CTAs of the fused SAI launch (0: one launch per sweep)
+    double *sai_gval = nullptr;  // [sai_gw][ns] G = I - M A (ELL)
+    int32_t *sai_gcol = nullptr; // [sai_gw][ns] its columns (-1: unused slot)
+    int sai_gw = 0;
+    double *sai_cb = nullptr;    // [ns] c = M b of the current step
     double sai_contraction = 0.0;
     double *d_r = nullptr;       // [ns] residual
     int *d_alpha = nullptr;      // device-side step counter for graph-replayed steps
