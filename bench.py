@@ -947,7 +947,7 @@ def run_sai_study(args):
             t.close()
         train = []
         cases = [("sphere81920_bmbie_d2_hard_plane", 5, (4, 4, 0), 2048),
-                 ("ellipsoid20480_bmbie_d2_hard_plane", 3, (7, 7, 0), 1024)]
+                 ("ellipsoid20480_bmbie_d2_hard_plane", 3, (7, 8, 0), 1024)]
         out["held_out"] = []
         for name, depth, fmm, nt in cases:
             w = workload(name, nt=nt)
@@ -955,7 +955,7 @@ def run_sai_study(args):
             res = {}
             X = {}
             for label, precond in (("jacobi", 0), ("learned_sai", 1)):
-                s = gpu_solver(w, precision=1, depth=depth, fmm=fmm, precond=precond)
+                s = gpu_solver(w, precision=4, depth=depth, fmm=fmm, precond=precond)
                 try:
                     if precond:
                         use, sweeps, q = abi.tdbem_set_precond(s.ctx, sai)

@@ -158,7 +158,12 @@ int tdbem_create(const tdbem_params *p, void *stream, tdbem_ctx **out)
     c->split = (p->precision >= 1);
     c->user = (cudaStream_t)stream;
     cudaGetDevice(&c->dev);
-    if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess) {
+    // the context's stream at the highest priority: the deferred far-field
+    // work of the FMM runs on a lower-priority second stream, and the block
+    // scheduler then serves the per-step kernels first
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (cudaStreamCreateWithPriority(&c->s, cudaStreamNonBlocking, hi_prio) != cudaSuccess) {
         delete c;
         return TDBEM_ERR_CUDA;
     }
@@ -521,6 +526,8 @@ static int step_impl(tdbem_ctx *c, int nsteps, const double *d_exc, int64_t exc_
         c->alpha = alpha;
         c->steps_total += 1;
     }
+    // the deferred far-field work of the last boundary is part of this call
+    if (c->fmm.on) TD_CUDA(fmm_join(c));
     return TDBEM_OK;
 }
 
@@ -558,6 +565,7 @@ static int graph_ready(tdbem_ctx *c)
         return fail(c, TDBEM_ERR_ARG, "graph-replayed FMM steps need a tensor-core precision (1-4)");
     if (c->sai_val) return fail(c, TDBEM_ERR_ARG, "graph-replayed steps use the Jacobi zero-lag solve");
     if (!c->d_alpha) TD_CUDA(dalloc(c, &c->d_alpha, 1));
+    TD_CUDA(fmm_join(c));
     return TDBEM_OK;
 }
 
@@ -897,6 +905,7 @@ int tdbem_checkpoint(const tdbem_ctx *cc, void *buf, size_t *len)
         return TDBEM_OK;
     }
     if (*len < need) return fail(c, TDBEM_ERR_ARG, "checkpoint buffer too small");
+    TD_CUDA(fmm_join(c));
     TD_CUDA(cudaStreamSynchronize(c->s));
     int64_t h[8] = {kCkptMagic, 1, c->ns, c->P.nt, c->alpha, c->P.algo, c->P.precision, c->fmm.far_k};
     char *o = (char *)buf;
@@ -920,6 +929,7 @@ int tdbem_restore(tdbem_ctx *c, const void *buf, size_t len)
     if (h[0] != kCkptMagic || h[1] != 1 || h[2] != c->ns || h[3] != c->P.nt || h[5] != c->P.algo ||
         h[6] != c->P.precision || h[4] < 0 || h[4] > c->P.nt - 1)
         return fail(c, TDBEM_ERR_ARG, "checkpoint of another problem or format");
+    TD_CUDA(fmm_join(c));
     int keep = c->alpha;
     c->alpha = (int)h[4];
     auto parts = ckpt_parts(c);
@@ -1006,6 +1016,7 @@ int tdbem_reset_stats(tdbem_ctx *c)
 int tdbem_sync(tdbem_ctx *c)
 {
     if (!c) return TDBEM_ERR_ARG;
+    TD_CUDA(fmm_join(c));
     TD_CUDA(cudaStreamSynchronize(c->s));
     TD_CUDA(cudaGetLastError());
     return check_flags(c);

@@ -677,13 +677,14 @@ __global__ void k_m2l_reduce(int nc, int P3, int P, int nblk, int mu, int nslot,
 }
 
 // The same reduction with coalesced reads (tensor-core forms): one CTA per
-// (observation cell, chunk of rows [r0, r0 + nrow), a multiple of P3); for
+// (observation cell, chunk of rows [r0, r0 + nrow) of the range [rb, re),
+// r0 and nrow multiples of P3); for
 // each pair in list order the CTA reads the chunk of the pair's product
 // contiguously and adds row a_c + rest to the double-float accumulator of
 // row perm_g(a_c) + rest in shared memory (the same additions in the same
 // order as k_m2l_reduce, so the same bits); a barrier between pairs.
-__global__ void k_m2l_reduce_smem(int nc, int P3, int P, int nblk, int mu, int nslot, int k, int nrow,
-                                  const int64_t *__restrict__ ooff, const int64_t *__restrict__ oidx,
+__global__ void k_m2l_reduce_smem(int nc, int P3, int P, int nblk, int mu, int nslot, int k, int nrow, int rb,
+                                  int re, const int64_t *__restrict__ ooff, const int64_t *__restrict__ oidx,
                                   const uint8_t *__restrict__ og, const int16_t *__restrict__ perm,
                                   const float *__restrict__ C, double *ring, StepWhen w)
 {
@@ -692,8 +693,8 @@ __global__ void k_m2l_reduce_smem(int nc, int P3, int P, int nblk, int mu, int n
     float *hi = acc, *lo = acc + nrow;
     const int R = nblk * P;
     const int O = blockIdx.x;
-    const int r0 = blockIdx.y * nrow;
-    const int n = min(nrow, R - r0);
+    const int r0 = rb + blockIdx.y * nrow;  // rows [rb, re), rb a multiple of P3
+    const int n = min(nrow, re - r0);
     const int64_t t0 = ooff[O];
     const int nt = (int)(ooff[O + 1] - t0);
     for (int e = threadIdx.x; e < n; e += blockDim.x) hi[e] = lo[e] = 0.f;
@@ -1065,14 +1066,18 @@ static size_t deriv_shm(int D, int P3, size_t el, int *cw)
 }
 
 // D = d + 1 (moments j = 0..d, distance powers e = 0..d, rows p = 0..d).
+// parts: bit 0 the time moments (they read the level's moments M), bit 1
+// the products and the assembly (they read only the moments' products).
 template <typename T, int D>
 static cudaError_t launch_deriv_d(int nc, int P3, int pt, int nslot, int k, int mu, const FmmLevel &V,
                                   const double *wt, const int16_t *perm, const int16_t *iperm, cudaStream_t s,
-                                  StepWhen w)
+                                  StepWhen w, int parts)
 {
     T *dm = reinterpret_cast<T *>(V.dmu), *Fp = reinterpret_cast<T *>(V.dF);
     const int bdim = std::max(128, (P3 + 31) / 32 * 32);
-    k_deriv_moments<T, D><<<(unsigned)V.np, 128, 0, s>>>(V.np, P3, pt, V.pS, V.pg, perm, wt, V.M, dm, V.dss, w);
+    if (parts & 1)
+        k_deriv_moments<T, D><<<(unsigned)V.np, 128, 0, s>>>(V.np, P3, pt, V.pS, V.pg, perm, wt, V.M, dm, V.dss, w);
+    if (!(parts & 2)) return cudaGetLastError();
     int cw = 32;
     const size_t shm = deriv_shm(D, P3, sizeof(T), &cw);
     if (shm > 48 * 1024) {
@@ -1089,13 +1094,13 @@ static cudaError_t launch_deriv_d(int nc, int P3, int pt, int nslot, int k, int 
 template <typename T>
 static cudaError_t launch_deriv(int d, int nc, int P3, int pt, int nslot, int k, int mu, const FmmLevel &V,
                                 const double *wt, const int16_t *perm, const int16_t *iperm, cudaStream_t s,
-                                StepWhen w)
+                                StepWhen w, int parts)
 {
     switch (d) {
-    case 1: return launch_deriv_d<T, 2>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
-    case 2: return launch_deriv_d<T, 3>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
-    case 3: return launch_deriv_d<T, 4>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
-    default: return launch_deriv_d<T, 5>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w);
+    case 1: return launch_deriv_d<T, 2>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w, parts);
+    case 2: return launch_deriv_d<T, 3>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w, parts);
+    case 3: return launch_deriv_d<T, 4>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w, parts);
+    default: return launch_deriv_d<T, 5>(nc, P3, pt, nslot, k, mu, V, wt, perm, iperm, s, w, parts);
     }
 }
 
@@ -1214,31 +1219,39 @@ static int sym_decompose(const int o[3], int c[3])
 // of its operator stack that are not all zero (bm: largest |entry| of every
 // (class, stack block)), times its columns in chunks of bn; *flops = the
 // algorithmic flops of the tiles kept.
+// The tiles whose rows start in the first near-future block (r0 < P) come
+// first (*nu of them, *flops_u their flops), then the others.
 static std::vector<TcTile> m2l_tiles(const Fmm &F, const FmmLevel &V, int bn, const std::vector<double> &bm,
-                                     double *flops)
+                                     double *flops, int *nu = nullptr, double *flops_u = nullptr)
 {
     std::vector<TcTile> t;
     double fl = 0.0;
-    for (int ci = 0; ci < V.ncls; ++ci) {
-        const int64_t n = V.cbase[ci + 1] - V.cbase[ci];
-        if (n == 0) continue;
-        for (int r0 = 0; r0 < F.R; r0 += kTcBM) {
-            const int r1 = std::min(F.R, r0 + kTcBM);
-            bool zero = true;
-            for (int blk = r0 / F.P; blk <= (r1 - 1) / F.P; ++blk)
-                if (bm[(size_t)ci * F.ngb + blk] != 0.0) zero = false;
-            if (zero) continue;  // these rows of the products stay zero
-            fl += 2.0 * (r1 - r0) * F.P * (double)n;
-            for (int64_t j0 = 0; j0 < n; j0 += bn)
-                t.push_back({ci * F.Rp + r0, (int32_t)(V.cbase[ci] + j0), r1 - r0, (int32_t)std::min<int64_t>(bn, n - j0),
-                             (V.cbase[ci] + j0) * (int64_t)F.R + r0});
+    if (flops_u) *flops_u = 0.0;
+    for (int part = 0; part < 2; ++part) {
+        for (int ci = 0; ci < V.ncls; ++ci) {
+            const int64_t n = V.cbase[ci + 1] - V.cbase[ci];
+            if (n == 0) continue;
+            for (int r0 = 0; r0 < F.R; r0 += kTcBM) {
+                if ((r0 < F.P) != (part == 0)) continue;
+                const int r1 = std::min(F.R, r0 + kTcBM);
+                bool zero = true;
+                for (int blk = r0 / F.P; blk <= (r1 - 1) / F.P; ++blk)
+                    if (bm[(size_t)ci * F.ngb + blk] != 0.0) zero = false;
+                if (zero) continue;  // these rows of the products stay zero
+                fl += 2.0 * (r1 - r0) * F.P * (double)n;
+                if (part == 0 && flops_u) *flops_u += 2.0 * (r1 - r0) * F.P * (double)n;
+                for (int64_t j0 = 0; j0 < n; j0 += bn)
+                    t.push_back({ci * F.Rp + r0, (int32_t)(V.cbase[ci] + j0), r1 - r0,
+                                 (int32_t)std::min<int64_t>(bn, n - j0), (V.cbase[ci] + j0) * (int64_t)F.R + r0});
+            }
         }
+        if (part == 0 && nu) *nu = (int)t.size();
     }
     *flops = fl;
     return t;
 }
 
-static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V, StepWhen w = StepWhen{})
+static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V, StepWhen w = StepWhen{}, int gsel = 0)
 {
     const Fmm &F = c->fmm;
     TcGemmArgs g{};
@@ -1255,7 +1268,7 @@ static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V, StepWhen w = StepWhe
     g.b_scale = F.f16 ? V.bscale : nullptr;
     g.ldc = F.R;
     g.C = V.C32;
-    g.tiles = V.tiles;
+    g.tiles = gsel == 2 ? V.tiles + V.ntiles_u : V.tiles;
     g.err = c->d_flag;
     g.when = w;
     return g;
@@ -1263,10 +1276,17 @@ static TcGemmArgs m2l_args(tdbem_ctx *c, const FmmLevel &V, StepWhen w = StepWhe
 
 // The products of one M2L application: every class's canonical operator
 // stack times its gathered columns.
-static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V, StepWhen w = StepWhen{})
+// gsel: 0 every tile; 1 the tiles of the first near-future block (rows
+// below P); 2 the others (the tile list keeps the first ones in front).
+static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V, StepWhen w = StepWhen{}, int gsel = 0)
 {
     Fmm &F = c->fmm;
-    if (c->split) return tc_gemm_launch(V.mapA, V.mapB, m2l_args(c, V, w), V.ntiles, V.tile_n, c->s);
+    if (c->split) {
+        const int nt = gsel == 0 ? V.ntiles : gsel == 1 ? V.ntiles_u : V.ntiles - V.ntiles_u;
+        // the deferred tiles run beside the history sums: half the SMs
+        return tc_gemm_launch(V.mapA, V.mapB, m2l_args(c, V, w, gsel), nt, V.tile_n, c->s, gsel == 2 ? 2 : 1);
+    }
+    if (gsel == 2) return cudaSuccess;  // the FP64 form's GEMMs run whole (no deferred part)
     if (w.alpha) return cudaErrorNotSupported;  // the FP64 form's library GEMMs cannot be predicated
     const double one = 1.0, zero = 0.0;
     for (int ci = 0; ci < V.ncls; ++ci) {
@@ -1360,7 +1380,7 @@ static cudaError_t m2l_tune(tdbem_ctx *c, FmmLevel &V, const std::vector<double>
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return err;
-    std::vector<TcTile> t = m2l_tiles(F, V, best, bm, &fl);
+    std::vector<TcTile> t = m2l_tiles(F, V, best, bm, &fl, &V.ntiles_u, &V.flops_u);
     F_TRY(cudaMemcpyAsync(V.tiles, t.data(), t.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
     F_TRY(tc_make_map(&V.mapB, V.Bt, (int64_t)F.ntb * V.np, F.Kp, best));
     V.tile_n = best;
@@ -1453,6 +1473,13 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         cublasSetStream(F.blas, c->s);
         cublasSetMathMode(F.blas, CUBLAS_DEFAULT_MATH);
     } else {
+        // the second stream of the deferred boundary work (fmm_boundary), at
+        // the lowest priority
+        int lo_prio = 0, hi_prio = 0;
+        F_TRY(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+        F_TRY(cudaStreamCreateWithPriority(&F.side, cudaStreamNonBlocking, lo_prio));
+        F_TRY(cudaEventCreateWithFlags(&F.ev_urgent, cudaEventDisableTiming));
+        F_TRY(cudaEventCreateWithFlags(&F.ev_deferred, cudaEventDisableTiming));
         // tensor-core forms: BF16 terms of operators and moments, and the
         // products (A term, B term) kept: all with s + t < nterm
         // (precision 4: two FP16 terms with power-of-two scales, products
@@ -1725,19 +1752,26 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     return cudaStreamSynchronize(c->s);
 }
 
-// Far field at the boundary after leaf interval k (every source of J_k is
-// known): P2M, M2M + M2L up the levels whose interval ended, L2L down the
-// levels whose interval starts, and L2P of the leaf local of I_{k+1}.
-//
-// graph = true (capture of a graph-replayed step): every pass of every level
-// is launched, each kernel reading the step from c->d_alpha and deciding on
-// the device whether it runs (StepWhen); k is not used.  The phase timers
-// and counters of plain stepping are left alone.
-cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
+// Parts of a boundary's far-field work (fmm_boundary_part).
+enum { FB_URGENT = 1, FB_DEFERRED = 2, FB_ALL = 3 };
+
+// The far-field work at the boundary after leaf interval k, or a part of it:
+//   urgent (what the next L_t steps' far field needs): P2M, and per level
+//     whose interval ended the gather, the GEMM tiles of the first
+//     near-future block, its reduction into the local L_{k+1}, the time
+//     moments of the exact rows, M2M into the parent and the clearing of
+//     the level's moments; the L2L of the levels whose interval starts; L2P;
+//   deferred (needed from the next boundary on): the GEMM tiles and the
+//     reduction of the near-future blocks 2..mu, the exact rows (products,
+//     assembly into L_{k+mu+1} and G) and the recurrence of Formula 1.
+// graph = true: every pass of every level is launched, each kernel deciding
+// on the device whether it runs (StepWhen); k is not used; part = FB_ALL.
+static cudaError_t fmm_boundary_part(tdbem_ctx *c, int k, bool graph, int part)
 {
     Fmm &F = c->fmm;
     const int L = F.L, d = c->P.d, P = F.P;
     cudaStream_t s = c->s;
+    const bool urgent = part & FB_URGENT, deferred = part & FB_DEFERRED;
     const double pref = 1.0 / (4.0 * M_PI * pow(c->cdt, d));
     const TreeLevel &TL = c->tree.levels[L];
     auto when = [&](int span) {
@@ -1750,15 +1784,15 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
         }
         return w;
     };
-    if (!graph) c->far_kernels += 2;
-    {
+    if (urgent) {
+        if (!graph) c->far_kernels += 2;
         const int64_t nx = (int64_t)c->ns * F.pt;
         k_p2m_time<<<(int)((nx + 255) / 256), 256, 0, s>>>(c->ns, F.pt, F.Lt, k, d, c->P.nt - 2, c->tree.perm, c->d_q,
                                                            c->d_u, F.wk, F.tl, F.Tq, F.Tu, when(1));
         k_p2m_moments<<<dim3(TL.nc, (P + 255) / 256), 256, 0, s>>>(F.P3, P, TL.cstart, c->tree.perm, F.At, F.As, F.Tq,
                                                                    F.Tu, pref, F.lev[L].M, when(1));
+        F_TRY(cudaGetLastError());
     }
-    F_TRY(cudaGetLastError());
     size_t shm = 2 * P * sizeof(double);
     for (int l = L; l >= 2; --l) {
         int span = 1 << (L - l);
@@ -1769,79 +1803,104 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
         const TreeLevel &T = c->tree.levels[l];
         // M2L for source interval kl of this level: gather (permuted by each
         // column's symmetry), one GEMM per symmetry class, per-cell
-        // reduction into the locals (near future) and G
+        // reduction into the locals (near future), exact rows
         if (V.np > 0) {
             cudaEvent_t ev = nullptr;
             if (!graph) phase_begin(c, &ev);
-            const int64_t n = V.np * P;
-            const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-            if (!graph) c->far_kernels += 3;  // gather, products, reduction
-            if (F.f16) {
-                k_cell_scale<<<V.nc, 256, 0, s>>>(P, V.M, V.cexp, w);
-                k_m2l_gather_f16<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, V.pS, V.pg, F.perm, V.M, V.cexp, V.Bt,
-                                                     V.bscale, w);
-            } else if (c->split)
-                k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt, w);
-            else
-                k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf, w);
-            F_TRY(cudaGetLastError());
+            if (urgent) {
+                const int64_t n = V.np * P;
+                const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+                if (!graph) c->far_kernels += 1;
+                if (F.f16) {
+                    k_cell_scale<<<V.nc, 256, 0, s>>>(P, V.M, V.cexp, w);
+                    k_m2l_gather_f16<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, V.pS, V.pg, F.perm, V.M, V.cexp, V.Bt,
+                                                         V.bscale, w);
+                } else if (c->split)
+                    k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt,
+                                                            w);
+                else
+                    k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf, w);
+                F_TRY(cudaGetLastError());
+            }
+            // GEMM tiles: all (FB_ALL), or those of the first block / the rest
+            const int gsel = (part == FB_ALL) ? 0 : (urgent ? 1 : 2);
             if (graph) {
-                F_TRY(m2l_products(c, V, w));
+                F_TRY(m2l_products(c, V, w, gsel));
             } else {
                 cudaEvent_t eg;
                 phase_begin(c, &eg);
-                F_TRY(m2l_products(c, V, w));
+                F_TRY(m2l_products(c, V, w, gsel));
                 phase_end(c, PH_GEMM, eg);
-                c->launches[PH_GEMM] += c->split ? 1 : V.ncls;
-                c->gemm_tc_flops += V.flops_app * (c->split ? F.nprod : 1);
+                c->launches[PH_GEMM] += c->split ? 1 : (gsel == 2 ? 0 : V.ncls);
+                c->gemm_tc_flops += (gsel == 0 ? V.flops_app : gsel == 1 ? V.flops_u : V.flops_app - V.flops_u) *
+                                    (c->split ? F.nprod : 1);
             }
+            if (!graph) c->far_kernels += 1;
             if (c->split) {
-                const int nrow = reduce_rows(F.P3, F.R);
-                const size_t shm = 2 * sizeof(float) * (size_t)nrow;
-                if (shm > 48 * 1024)
-                    F_TRY(cudaFuncSetAttribute(k_m2l_reduce_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-                k_m2l_reduce_smem<<<dim3(V.nc, (F.R + nrow - 1) / nrow), 512, shm, s>>>(
-                    V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, nrow, V.ooff, V.oidx, V.og, F.perm, V.C32, V.ring, w);
-            } else
+                // rows [0, P): the first block (urgent); [P, R): blocks 2..mu
+                const int rb = urgent ? 0 : P, re = deferred ? F.R : P;
+                if (re > rb) {
+                    const int nrow = reduce_rows(F.P3, re - rb);
+                    const size_t rshm = 2 * sizeof(float) * (size_t)nrow;
+                    if (rshm > 48 * 1024)
+                        F_TRY(cudaFuncSetAttribute(k_m2l_reduce_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)rshm));
+                    k_m2l_reduce_smem<<<dim3(V.nc, (re - rb + nrow - 1) / nrow), 512, rshm, s>>>(
+                        V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, nrow, rb, re, V.ooff, V.oidx, V.og, F.perm, V.C32,
+                        V.ring, w);
+                }
+            } else {
                 k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx,
                                                           V.og, F.iperm, V.Cbuf, V.ring, V.G, w);
+            }
             F_TRY(cudaGetLastError());
             // the block L_{k+mu+1,k} and the derivative contributions G (exact
-            // low-rank form of Eq. U_expand)
+            // low-rank form of Eq. U_expand): moments now, the rest deferred
+            const int dparts = (urgent ? 1 : 0) | (deferred ? 2 : 0);
             if (c->split)
-                F_TRY(launch_deriv<float2>(d, V.nc, F.P3, F.pt, F.nslot, kl, F.mu, V, F.wt, F.perm, F.iperm, s, w));
+                F_TRY(launch_deriv<float2>(d, V.nc, F.P3, F.pt, F.nslot, kl, F.mu, V, F.wt, F.perm, F.iperm, s, w,
+                                           dparts));
             else
-                F_TRY(launch_deriv<double>(d, V.nc, F.P3, F.pt, F.nslot, kl, F.mu, V, F.wt, F.perm, F.iperm, s, w));
+                F_TRY(launch_deriv<double>(d, V.nc, F.P3, F.pt, F.nslot, kl, F.mu, V, F.wt, F.perm, F.iperm, s, w,
+                                           dparts));
             if (!graph) {
-                c->far_kernels += 3;
+                c->far_kernels += (urgent ? 1 : 0) + (deferred ? 2 : 0);
                 phase_end(c, PH_M2L, ev);
-                c->launches[PH_M2L] += 1;
-                c->m2l_flops += V.flops_app + V.flops_deriv;
+                if (urgent) {
+                    c->launches[PH_M2L] += 1;
+                    c->m2l_flops += V.flops_app + V.flops_deriv;
+                }
             }
-        } else if (!graph) {
+        } else if (!graph && deferred) {
             // (G of a level without pairs stays zero from its allocation on)
             F_TRY(cudaMemsetAsync(V.G, 0, (size_t)d * V.nc * P * sizeof(double), s));
         }
         int64_t n = (int64_t)V.nc * P;
-        if (!graph) ++c->far_kernels;
-        k_m2l_recurrence<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
-            n, d, F.mu, F.nslot, kl, V.G, V.D, V.A, V.ring, V.Tlen, w);
-        F_TRY(cudaGetLastError());
-        // M2M into the parent, then clear this level's accumulator
-        if (l > 2) {
-            FmmLevel &Pv = F.lev[l - 1];
-            const TreeLevel &PT = c->tree.levels[l - 1];
+        if (deferred) {
             if (!graph) ++c->far_kernels;
-            k_m2m<<<Pv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, PT.ckey, V.nc, T.ckey, V.M, Pv.M, V.Sm, F.Tm, kl & 1, w);
+            k_m2l_recurrence<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+                n, d, F.mu, F.nslot, kl, V.G, V.D, V.A, V.ring, V.Tlen, w);
             F_TRY(cudaGetLastError());
         }
-        if (graph) {
-            k_zero_when<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(n, V.M, w);
-            F_TRY(cudaGetLastError());
-        } else {
-            F_TRY(cudaMemsetAsync(V.M, 0, (size_t)V.nc * P * sizeof(double), s));
+        if (urgent) {
+            // M2M into the parent, then clear this level's accumulator
+            if (l > 2) {
+                FmmLevel &Pv = F.lev[l - 1];
+                const TreeLevel &PT = c->tree.levels[l - 1];
+                if (!graph) ++c->far_kernels;
+                k_m2m<<<Pv.nc, 128, shm, s>>>(F.ps, F.pt, Pv.nc, PT.ckey, V.nc, T.ckey, V.M, Pv.M, V.Sm, F.Tm, kl & 1,
+                                              w);
+                F_TRY(cudaGetLastError());
+            }
+            if (graph) {
+                k_zero_when<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(n, V.M, w);
+                F_TRY(cudaGetLastError());
+            } else {
+                F_TRY(cudaMemsetAsync(V.M, 0, (size_t)V.nc * P * sizeof(double), s));
+            }
         }
     }
+    if (!urgent) return cudaSuccess;
     // L2L into the levels whose interval starts at leaf interval k + 1
     for (int l = 2; l < L; ++l) {
         int span = 1 << (L - l - 1);  // leaf intervals per level-(l+1) interval
@@ -1862,12 +1921,61 @@ cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
     return cudaGetLastError();
 }
 
+// Far field at the boundary after leaf interval k (every source of J_k is
+// known): P2M, M2M + M2L up the levels whose interval ended, L2L down the
+// levels whose interval starts, and L2P of the leaf local of I_{k+1}.
+//
+// Plain stepping in a tensor-core form overlaps: the urgent part runs on
+// the context's stream (after the previous boundary's deferred part), the
+// deferred part on the second stream F.side, under the history sums of the
+// following steps.  The two parts write disjoint rows of the locals (block
+// 1 vs blocks 2..mu+1), and the next urgent part waits for the deferred one
+// before it touches any state the deferred part uses, so the results equal
+// the sequential order's bit for bit.
+//
+// graph = true (capture of a graph-replayed step): sequential, every pass of
+// every level launched, each kernel reading the step from c->d_alpha and
+// deciding on the device whether it runs (StepWhen); the phase timers and
+// counters of plain stepping are left alone.
+cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
+{
+    Fmm &F = c->fmm;
+    if (graph || !F.side) return fmm_boundary_part(c, k, graph, FB_ALL);
+    F_TRY(cudaStreamWaitEvent(c->s, F.ev_deferred, 0));
+    F_TRY(fmm_boundary_part(c, k, false, FB_URGENT));
+    F_TRY(cudaEventRecord(F.ev_urgent, c->s));
+    F_TRY(cudaStreamWaitEvent(F.side, F.ev_urgent, 0));
+    cudaStream_t keep = c->s;
+    c->s = F.side;
+    cudaError_t e = fmm_boundary_part(c, k, false, FB_DEFERRED);
+    c->s = keep;
+    F_TRY(e);
+    F_TRY(cudaEventRecord(F.ev_deferred, F.side));
+    return cudaSuccess;
+}
+
+// Orders the context's stream after the last deferred far-field work (before
+// the FMM state is read, saved or the call returns).
+cudaError_t fmm_join(tdbem_ctx *c)
+{
+    Fmm &F = c->fmm;
+    if (!F.side) return cudaSuccess;
+    return cudaStreamWaitEvent(c->s, F.ev_deferred, 0);
+}
+
 #undef F_TRY
 
 void fmm_free(tdbem_ctx *c)
 {
     if (c->fmm.blas) cublasDestroy(c->fmm.blas);
     c->fmm.blas = nullptr;
+    if (c->fmm.side) {
+        cudaStreamSynchronize(c->fmm.side);
+        cudaStreamDestroy(c->fmm.side);
+        cudaEventDestroy(c->fmm.ev_urgent);
+        cudaEventDestroy(c->fmm.ev_deferred);
+        c->fmm.side = nullptr;
+    }
 }
 
 }  // namespace tdbem

@@ -359,7 +359,7 @@ size_t tc_smem_bytes(int nta, int ntb, int bn, int nstage)
 }
 
 cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const TcGemmArgs &a, int ntiles, int bn,
-                           cudaStream_t s)
+                           cudaStream_t s, int sm_div)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (a.nstage < 1 || a.nta < 1 || a.nta > kTcMaxTerms || a.ntb < 1 || a.ntb > kTcMaxTerms || a.nprod < 1 ||
@@ -380,7 +380,7 @@ cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const T
     }
     TcGemmArgs g = a;
     g.ntiles = ntiles;
-    const int grid = std::min(ntiles, nsm);
+    const int grid = std::min(ntiles, std::max(1, nsm / std::max(sm_div, 1)));
     cudaError_t e;
     if (bn == 128) {
         e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBudget);

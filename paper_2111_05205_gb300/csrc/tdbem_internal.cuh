@@ -143,8 +143,9 @@ struct TcGemmArgs {
 cudaError_t tc_make_map(CUtensorMap *map, const void *base, int64_t rows, int kp, int box_rows);
 int tc_stages(int nta, int ntb, int bn);
 size_t tc_smem_bytes(int nta, int ntb, int bn, int nstage);
+// sm_div: the persistent grid takes 1/sm_div of the SMs (1: all)
 cudaError_t tc_gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, const TcGemmArgs &a, int ntiles, int bn,
-                           cudaStream_t s);
+                           cudaStream_t s, int sm_div = 1);
 
 // One level of the space-time FMM (device arrays; levels 2..L).
 //
@@ -197,8 +198,10 @@ struct FmmLevel {
     float *bscale = nullptr;     // scaled FP16 form: [np] column scales of the moment terms
     int *cexp = nullptr;         // scaled FP16 form: [nc] scale exponent of each cell's moment
     float *C32 = nullptr;        // [np][mu P] products
-    TcTile *tiles = nullptr;     // [ntiles] GEMM tiles (zero operator blocks skipped)
-    int ntiles = 0;
+    TcTile *tiles = nullptr;     // [ntiles] GEMM tiles (zero operator blocks skipped); the ntiles_u
+    int ntiles = 0;              // tiles of the first near-future block's rows come first
+    int ntiles_u = 0;
+    double flops_u = 0;          // algorithmic flops of those tiles
     int tile_n = 128;            // tile width chosen by the setup-time tuner
     std::vector<std::pair<int, float>> tune;  // (tile width, ms) measured at setup
     CUtensorMap mapA{}, mapB{};
@@ -227,6 +230,10 @@ struct Fmm {
     double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
     double *Tq = nullptr, *Tu = nullptr;    // [ns][pt] P2M time sums of the folded histories (sorted order)
     int far_k = -1;                         // leaf interval the far field belongs to
+    // plain stepping in the tensor-core forms: the deferred part of each
+    // boundary's work runs on this second stream (fmm_boundary)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_urgent = nullptr, ev_deferred = nullptr;
 };
 
 struct Pending {
@@ -361,6 +368,7 @@ cudaError_t build_near_lists(tdbem_ctx *c);
 // Space-time FMM (fmm.cu)
 cudaError_t fmm_setup(tdbem_ctx *c, std::string &why);
 cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph = false);
+cudaError_t fmm_join(tdbem_ctx *c);
 // Phase timer hooks for fmm.cu (events on the context's stream).
 void phase_begin(tdbem_ctx *c, cudaEvent_t *e);
 void phase_end(tdbem_ctx *c, int phase, cudaEvent_t e);
