@@ -64,6 +64,18 @@ def test_sphere_refinement_reduces_error():
     assert e320 < 0.7 * e80
 
 
+def test_sphere_refinement_bmbie_d2_neumann():
+    """The benchmark's formulation (Burton-Miller, d = 2, Neumann) against the
+    closed-form sphere on 80 -> 320 -> 1280 elements (c dt = half the mean
+    edge): the error must fall at the discretisation rate, by more than 2x
+    per refinement (measured 0.476 -> 0.174 -> 0.051).  A wrong sign or
+    factor in the hypersingular or the time-derivative part of the
+    Burton-Miller kernels leaves an error that does not shrink."""
+    e = [_sphere_error("sphere%d_bmbie_d2_neumann_uniform" % ns) for ns in (80, 320, 1280)]
+    assert e[1] < 0.45 * e[0] and e[2] < 0.45 * e[1], e
+    assert e[2] < 0.07, e
+
+
 @pytest.mark.parametrize("name", ["sphere80_obie_d1_dirichlet_uniform", "sphere80_obie_d2_neumann_uniform"])
 def test_compact_equals_tau_form(name):
     w = workload(name, nt=24)
