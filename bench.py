@@ -203,6 +203,41 @@ def run_ours(args):
     return run_fmm(args)
 
 
+def _rooflines(st, nsteps, prec):
+    """Roofline objects of the history sum (HBM) and of the tcgen05 GEMM
+    (tensor pipe) from one timed region's stats; the first of the returned
+    triple is the kernel with the most device time per step."""
+    bf16, bf_kind = _bf16_peak()
+    gemm_ms = st["ms_gemm"] / max(st["launches_gemm"], 1)
+    nprod = max(st["m2l_products"], 1)
+    if prec:
+        tc = st["gemm_tc_flops"] / (st["ms_gemm"] * 1e-3) / 1e12 if st["ms_gemm"] > 0 else 0.0
+        gemm_obj = {
+            "bound": "tensor", "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16,
+            "traffic": None, "kernel": "k_tc_gemm (M2L, tcgen05)",
+            "peak_source": bf_kind + " bf16 burst" + (" (FP16 has the same nominal dense rate)" if prec == 4 else ""),
+            "flops_per_launch": st["gemm_tc_flops"] / max(st["launches_gemm"], 1), "avg_launch_ms": gemm_ms,
+            "flops": "16-bit tensor-pipe flops the split needs: %d products x 2 P per kept operator row and pair "
+                     "(K and tile padding not counted)" % nprod,
+            "useful_tflops": tc / nprod, "useful_frac": tc / nprod / bf16}
+    else:
+        f64 = st["gemm_tc_flops"] / (st["ms_gemm"] * 1e-3) / 1e12 if st["ms_gemm"] > 0 else 0.0
+        gemm_obj = {"bound": "alu", "achieved": f64, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": f64 / FP64_TFLOPS, "traffic": None, "kernel": "M2L FP64 DGEMM",
+                    "peak_source": "FP64 FMA probe (measured)"}
+    hbm, peak_kind = _peaks()
+    near_ms = st["ms_near"] / max(st["launches_near"], 1)
+    near_obj = {"bound": "hbm", "kernel": "k_near_sum (near lists)", "avg_launch_ms": near_ms,
+                "bytes_per_launch": st["near_bytes_per_step"],
+                "achieved": st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9, "peak": hbm,
+                "unit": "GB/s", "frac": st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9 / hbm,
+                "traffic": _traffic(st), "peak_source": peak_kind + " copy bandwidth"}
+    near_share, gemm_share = st["ms_near"] / nsteps, st["ms_gemm"] / nsteps
+    dom = dict(near_obj if near_share >= gemm_share else gemm_obj)
+    dom["ms_per_step"] = max(near_share, gemm_share)
+    return dom, near_obj, gemm_obj
+
+
 def run_fmm(args):
     """The headline: the space-time FMM (mixed form by default) on the
     benchmark workload, timed over whole cycles of its interval pattern,
@@ -254,6 +289,16 @@ def run_fmm(args):
     ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / nsteps
     e2e = _e2e(abi, torch, ctx, w, args.warmup, nsteps)
+    # the same steps once more with every far-field pass in order on one
+    # stream, so that each kernel's own rate can be read (the headline's
+    # timed region overlaps the deferred far-field work with the history sums)
+    st_alone, ms_alone = None, None
+    if prec and abi.tdbem_steps_done(ctx) + nsteps <= w.nt - 1:
+        abi.tdbem_set_overlap(ctx, 0)
+        abi.tdbem_reset_stats(ctx)
+        ms_alone = _timed(abi, torch, ctx, nsteps) / nsteps
+        st_alone = s.stats()
+        abi.tdbem_set_overlap(ctx, 1)
     out = {
         "metric": METRIC, "value": world * 1000.0 / ms_step, "unit": "time-steps/s", "n_gpus": world,
         "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -270,41 +315,19 @@ def run_fmm(args):
                          "exceed the 129 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
     }
-    bf16, bf_kind = _bf16_peak()
-    gemm_ms = st["ms_gemm"] / max(st["launches_gemm"], 1)
-    nprod = max(st["m2l_products"], 1)
-    if prec:
-        tc = st["gemm_tc_flops"] / (st["ms_gemm"] * 1e-3) / 1e12 if st["ms_gemm"] > 0 else 0.0
-        gemm_obj = {
-            "bound": "tensor", "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16,
-            "traffic": None, "kernel": "k_tc_gemm (M2L, tcgen05)",
-            "peak_source": bf_kind + " bf16 burst" + (" (FP16 has the same nominal dense rate)" if prec == 4 else ""),
-            "flops_per_launch": st["gemm_tc_flops"] / max(st["launches_gemm"], 1), "avg_launch_ms": gemm_ms,
-            "flops": "16-bit tensor-pipe flops the split needs: %d products x 2 P per kept operator row and pair "
-                     "(K and tile padding not counted)" % nprod,
-            "useful_tflops": tc / nprod, "useful_frac": tc / nprod / bf16}
-    else:
-        f64 = st["gemm_tc_flops"] / (st["ms_gemm"] * 1e-3) / 1e12 if st["ms_gemm"] > 0 else 0.0
-        gemm_obj = {"bound": "alu", "achieved": f64, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": f64 / FP64_TFLOPS, "traffic": None, "kernel": "M2L FP64 DGEMM",
-                    "peak_source": "FP64 FMA probe (measured)"}
-    hbm, peak_kind = _peaks()
-    near_ms = st["ms_near"] / max(st["launches_near"], 1)
-    near_obj = {"bound": "hbm", "kernel": "k_near_sum (near lists)", "avg_launch_ms": near_ms,
-                "bytes_per_launch": st["near_bytes_per_step"],
-                "achieved": st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9, "peak": hbm,
-                "unit": "GB/s", "frac": st["near_bytes_per_step"] / (near_ms * 1e-3) / 1e9 / hbm,
-                "traffic": _traffic(st), "peak_source": peak_kind + " copy bandwidth"}
-    # the dominant kernel of the step (device time per step) carries "roofline"
-    near_share, gemm_share = st["ms_near"] / nsteps, st["ms_gemm"] / nsteps
-    out["roofline"] = dict(near_obj if near_share >= gemm_share else gemm_obj)
-    out["roofline"]["ms_per_step"] = max(near_share, gemm_share)
-    out["near_roofline"] = near_obj
-    out["m2l_gemm_roofline"] = gemm_obj
+    out["roofline"], out["near_roofline"], out["m2l_gemm_roofline"] = _rooflines(st, nsteps, prec)
+    if st_alone is not None:
+        r = _rooflines(st_alone, nsteps, prec)
+        out["kernels_alone"] = {
+            "ms_per_step": ms_alone, "near_roofline": r[1], "m2l_gemm_roofline": r[2],
+            "note": "the same steps timed again with every far-field pass in order on the context's stream "
+                    "(tdbem_set_overlap 0): each kernel's rate without the overlapped far-field work beside it"}
     out["phases_ms_per_step"] = {
         "m2l": st["ms_m2l"] / nsteps, "m2l_gemm": st["ms_gemm"] / nsteps,
         "far_total": st["ms_far"] / nsteps, "near": st["ms_near"] / nsteps, "solve": st["ms_solve"] / nsteps,
-        "solve_sweeps": st["solve_iters"], "m2l_useful_tflops": st["m2l_flops"] / max(st["ms_m2l"], 1e-12) / 1e9}
+        "solve_sweeps": st["solve_iters"], "m2l_useful_tflops": st["m2l_flops"] / max(st["ms_m2l"], 1e-12) / 1e9,
+        "note": "phase times on their own streams: the deferred far-field work (M2L blocks 2..mu, exact rows, "
+                "recurrence) runs beside the history sums, so the phases overlap"}
     out["m2l_tile_n_by_level"] = st["m2l_tile_n"][:args.depth + 1]
     out["gpu_launches"] = int(st["launches_near"] + st["launches_solve"] + st["launches_far_kernels"])
     if rank == 0 and args.accuracy:

@@ -390,6 +390,16 @@ int tdbem_reset_stats(tdbem_ctx *ctx);
  * error (divergence guard) raised since the last check. */
 int tdbem_sync(tdbem_ctx *ctx);
 
+/* Schedule of the FMM's far field in plain stepping (tensor-core forms):
+ * overlap = 1 (the default) runs the part of each leaf-interval boundary's
+ * work that later boundaries need (M2L blocks 2..mu, the exact rows, the
+ * recurrence of Formula 1) on a second, lower-priority stream under the
+ * following steps' history sums; overlap = 0 runs every pass in order on the
+ * context's stream (every kernel then has the GPU to itself, e.g. to time
+ * it).  Results are the same bit for bit.  Takes effect at the next step;
+ * ERR_STATE before prepare. */
+int tdbem_set_overlap(tdbem_ctx *ctx, int32_t overlap);
+
 /* Zero-lag solve that allocates no device memory (the paper has no
  * counterpart: it is a service for callers that cannot call cudaMalloc at the
  * point where they solve, e.g. code that runs while someone else captures a

@@ -93,6 +93,7 @@ SIGNATURES = {
     "tdbem_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(tdbem_stats)]),
     "tdbem_reset_stats": (ctypes.c_int, [_P]),
     "tdbem_sync": (ctypes.c_int, [_P]),
+    "tdbem_set_overlap": (ctypes.c_int, [_P, _I]),
     "tdbem_zero_lag_solve_static": (ctypes.c_int, [_P, _P, _P, _I]),
     "tdbem_grid_barrier_probe": (ctypes.c_int, [_I, _I, ctypes.POINTER(_I)]),
     "tdbem_eval_field": (ctypes.c_int, [_P, _P, _I, _I, _I, _P]),
@@ -373,6 +374,10 @@ def tdbem_reset_stats(ctx):
 
 def tdbem_sync(ctx):
     _check(ctx, lib().tdbem_sync(ctx))
+
+
+def tdbem_set_overlap(ctx, overlap):
+    _check(ctx, lib().tdbem_set_overlap(ctx, int(overlap)))
 
 
 def tdbem_zero_lag_solve_static(ctx, b, x, on_device=False):

@@ -129,6 +129,7 @@ int check_flags(tdbem_ctx *c)
     TD_CUDA(cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f & 1) return fail(c, TDBEM_ERR_DIVERGED, "non-finite solution value (divergence guard)");
     if (f & 8) return fail(c, TDBEM_ERR_TIMEOUT, "M2L tensor-core GEMM: a pipeline wait timed out");
+    if (f & 16) return fail(c, TDBEM_ERR_TIMEOUT, "history sum: a staged coefficient copy wait timed out");
     if (f & 4) {
         // a grid barrier of the fused solve gave up waiting: reset it and
         // solve with one launch per sweep from now on
@@ -1010,6 +1011,15 @@ int tdbem_reset_stats(tdbem_ctx *c)
     c->m2l_flops = 0.0;
     c->gemm_tc_flops = 0.0;
     c->far_kernels = 0;
+    return TDBEM_OK;
+}
+
+int tdbem_set_overlap(tdbem_ctx *c, int32_t overlap)
+{
+    if (!c || (overlap != 0 && overlap != 1)) return TDBEM_ERR_ARG;
+    if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "overlap before prepare");
+    TD_CUDA(fmm_join(c));
+    c->fmm.overlap = overlap != 0;
     return TDBEM_OK;
 }
 

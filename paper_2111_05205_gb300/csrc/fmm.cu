@@ -1940,7 +1940,7 @@ static cudaError_t fmm_boundary_part(tdbem_ctx *c, int k, bool graph, int part)
 cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph)
 {
     Fmm &F = c->fmm;
-    if (graph || !F.side) return fmm_boundary_part(c, k, graph, FB_ALL);
+    if (graph || !F.side || !F.overlap) return fmm_boundary_part(c, k, graph, FB_ALL);
     F_TRY(cudaStreamWaitEvent(c->s, F.ev_deferred, 0));
     F_TRY(fmm_boundary_part(c, k, false, FB_URGENT));
     F_TRY(cudaEventRecord(F.ev_urgent, c->s));

@@ -234,6 +234,7 @@ struct Fmm {
     // boundary's work runs on this second stream (fmm_boundary)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_urgent = nullptr, ev_deferred = nullptr;
+    bool overlap = true;                    // tdbem_set_overlap
 };
 
 struct Pending {

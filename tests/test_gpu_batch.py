@@ -219,3 +219,39 @@ def test_batch_of_uneven_nt():
     finally:
         for s in sols:
             s.close()
+
+
+def test_overlapped_far_field_equals_sequential():
+    """Plain FMM stepping runs the part of each boundary's far-field work
+    that only later boundaries need on a second stream, beside the following
+    steps; the sequential schedule (tdbem_set_overlap 0) gives the same
+    history bit for bit, also when the schedule changes mid-march and across
+    checkpoint/restore."""
+    _need_gpu()
+    from paper_2111_05205_gb300 import abi
+    w = case("sphere1280_bmbie_d2_neumann_uniform", nt=81)
+    a = gpu_solver(w, precision=4, depth=3, fmm=(3, 3, 0))
+    b = gpu_solver(w, precision=4, depth=3, fmm=(3, 3, 0))
+    try:
+        abi.tdbem_set_overlap(b.ctx, 0)
+        abi.tdbem_step(a.ctx, 40)
+        blob = abi.tdbem_checkpoint(a.ctx)
+        abi.tdbem_step(a.ctx, 40)
+        abi.tdbem_step(b.ctx, 25)
+        abi.tdbem_set_overlap(b.ctx, 1)
+        abi.tdbem_step(b.ctx, 30)
+        abi.tdbem_set_overlap(b.ctx, 0)
+        abi.tdbem_step(b.ctx, 25)
+        ua, qa = a.solution()
+        ub, qb = b.solution()
+        assert np.abs(ua).max() > 0
+        assert np.array_equal(ua, ub) and np.array_equal(qa, qb)
+        # rewind the overlapped context and march again
+        abi.tdbem_restore(a.ctx, blob)
+        abi.tdbem_step(a.ctx, 40)
+        assert np.array_equal(a.solution()[0], ua)
+        with pytest.raises(abi.TdbemError):
+            abi.tdbem_set_overlap(a.ctx, 2)
+    finally:
+        a.close()
+        b.close()

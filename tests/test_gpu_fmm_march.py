@@ -1,0 +1,62 @@
+"""The whole FMM march against the oracle's direct march (Eq. linear, every
+element pair, FP64 in the oracle's C core): the space-time FMM replaces the
+far part of the history sum by its interpolated form (Sections 3-4), so the
+march differs from the direct one by the FMM's own interpolation error,
+which every FMM form must keep within 1e-3 relative L2 over all elements and
+steps.  The FP64 form, the FP32-grade BF16 split (precision 1) and the
+scaled FP16 split (precision 4, the benchmark's) are run on the same seeded
+inputs; the two tensor-core forms must also stay within 2e-4 of the FP64
+form (the rounding of their FP32-accumulated products, amplified by the
+far field's cancellation of terms 1e4-1e5 larger than itself: measured up
+to 6.2e-5 over the 120-step ellipsoid march).
+
+Measured (GB300): sphere, 1280 elements, Burton-Miller d = 2, uniform
+Neumann data, depth 2, ps = pt = 6: 1.42e-4 for every form; ellipsoid, 1280
+elements, the benchmark's formulation (sound-hard, plane pulse), depth 2,
+ps = pt = 7: 7.95e-4."""
+
+import numpy as np
+import pytest
+
+from oracle import mot
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("sphere1280_bmbie_d2_neumann_uniform", 81, 2, 6),
+    ("ellipsoid1280_bmbie_d2_hard_plane_s3", 120, 2, 7),
+]
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name,nt,depth,p", CASES)
+def test_fmm_march_within_1e3_of_the_oracle(name, nt, depth, p):
+    _need_gpu()
+    from tests.gpu_cases import gpu_solver
+    w = workload(name, nt=nt)
+    u0, q0 = mot.march(w)
+    X0 = u0 if w.bc == "neumann" else q0
+    assert np.abs(X0).max() > 0
+    X = {}
+    for prec in (0, 1, 4):
+        s = gpu_solver(w, precision=prec, depth=depth, fmm=(p, p, 0))
+        try:
+            s.step()
+            u, q = s.solution()
+        finally:
+            s.close()
+        X[prec] = u if w.bc == "neumann" else q
+        assert np.isfinite(X[prec]).all()
+        assert _rel(X[prec], X0) <= 1e-3, (prec, _rel(X[prec], X0))
+    for prec in (1, 4):
+        assert _rel(X[prec], X[0]) <= 2e-4, (prec, _rel(X[prec], X[0]))
