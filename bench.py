@@ -257,7 +257,7 @@ def run_fmm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build.build()
-    w = workload(args.workload)
+    w = workload(args.workload, nt=args.nt)
     prec = PREC[args.precision]
     stream = torch.cuda.current_stream().cuda_stream
     phi = np.full(w.ns, 1 if w.bc == "neumann" else 0, np.int8)
@@ -1017,6 +1017,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--nt", type=int, default=None, help="override the workload's number of steps")
     ap.add_argument("--cpu-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="f16x2", choices=["split", "fp64", "bf16x3", "bf16", "f16x2"])

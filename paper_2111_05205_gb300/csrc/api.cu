@@ -129,7 +129,6 @@ int check_flags(tdbem_ctx *c)
     TD_CUDA(cudaMemcpy(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f & 1) return fail(c, TDBEM_ERR_DIVERGED, "non-finite solution value (divergence guard)");
     if (f & 8) return fail(c, TDBEM_ERR_TIMEOUT, "M2L tensor-core GEMM: a pipeline wait timed out");
-    if (f & 16) return fail(c, TDBEM_ERR_TIMEOUT, "history sum: a staged coefficient copy wait timed out");
     if (f & 4) {
         // a grid barrier of the fused solve gave up waiting: reset it and
         // solve with one launch per sweep from now on

@@ -9,7 +9,6 @@ constexpr int kNearWarps = kNearThreads / 32;
 constexpr int kNearMinBlocks = 10;  // split form: 48 registers, 40 resident warps per SM (measured best)
 constexpr int kMaxFull = 4;         // full window slots handled by the unrolled bodies
 constexpr int kNearPrefetch = 2;  // blocks of a warp whose coefficients are asked of L2 ahead
-constexpr int kNearStages = 3;    // split form: blocks of a warp staged in shared memory ahead
 
 // Incident-wave term e_i(t_a) of the total-field equation: u_in (OBIE) or
 // (d/dn_x - c^-1 d/dt) u_in (BMBIE) for the plane pulse
@@ -96,17 +95,6 @@ __device__ __forceinline__ void near_fma(DF &dacc, double &acc, const typename N
     }
 }
 
-// A coefficient of the stream: from global memory with an evict-first hint,
-// or (SM) from the shared-memory stage a bulk copy brought it to.
-template <bool SM, typename V>
-__device__ __forceinline__ V near_ld(const V *p)
-{
-    if constexpr (SM)
-        return *p;
-    else
-        return __ldcs(p);
-}
-
 // One 32-pair block of a row: lane l holds pair (i, j_l) whose window is
 // lags g0_l .. g0_l + cnt_l - 1.  Slot s of the block is stored packed (the
 // lanes with cnt > s, in lane order) from offset o.  The N slots below the
@@ -119,7 +107,7 @@ __device__ __forceinline__ V near_ld(const V *p)
 // early steps a lag can reach before the first step (beta < 0): the
 // histories are allocated with as many zero rows before step 0 as the
 // largest stored lag, so those terms read zeros and add nothing.
-template <bool HU, bool HW, bool SPLIT, int N, bool SM>
+template <bool HU, bool HW, bool SPLIT, int N>
 __device__ __forceinline__ void near_slots(const typename NearV<SPLIT>::T *__restrict__ kub,
                                            const typename NearV<SPLIT>::T *__restrict__ kwb,
                                            const typename NearV<SPLIT>::T *__restrict__ hqb,
@@ -131,11 +119,11 @@ __device__ __forceinline__ void near_slots(const typename NearV<SPLIT>::T *__res
 #pragma unroll
     for (int s = 0; s < N; ++s) {
         if (HU) {
-            cu[s] = near_ld<SM>(kub + 32 * s + lane);
+            cu[s] = __ldcs(kub + 32 * s + lane);
             xu[s] = *(hqb - (int64_t)s * ns);
         }
         if (HW) {
-            cw[s] = near_ld<SM>(kwb + 32 * s + lane);
+            cw[s] = __ldcs(kwb + 32 * s + lane);
             xw[s] = *(hub - (int64_t)s * ns);
         }
     }
@@ -146,11 +134,11 @@ __device__ __forceinline__ void near_slots(const typename NearV<SPLIT>::T *__res
         if (on) {
             const int idx = 32 * N + __popc(mask & lt);
             if (HU) {
-                cu[N] = near_ld<SM>(kub + idx);
+                cu[N] = __ldcs(kub + idx);
                 xu[N] = *(hqb - (int64_t)N * ns);
             }
             if (HW) {
-                cw[N] = near_ld<SM>(kwb + idx);
+                cw[N] = __ldcs(kwb + idx);
                 xw[N] = *(hub - (int64_t)N * ns);
             }
         }
@@ -169,7 +157,7 @@ __device__ __forceinline__ void near_slots(const typename NearV<SPLIT>::T *__res
 // Slots s0 <= s < cmax of a block, one at a time, each located by a ballot
 // (blocks whose counts differ by more than one, or exceed the unrolled
 // range).
-template <bool HU, bool HW, bool SPLIT, bool SM>
+template <bool HU, bool HW, bool SPLIT>
 __device__ __forceinline__ void near_slots_rest(const typename NearV<SPLIT>::T *__restrict__ kub,
                                              const typename NearV<SPLIT>::T *__restrict__ kwb,
                                              const typename NearV<SPLIT>::T *__restrict__ hqb,
@@ -186,14 +174,14 @@ __device__ __forceinline__ void near_slots_rest(const typename NearV<SPLIT>::T *
         if (cnt > s) {
             const int idx = pos + __popc(mask & lt);
             const int64_t h = (int64_t)s * ns;
-            if (HU) near_fma<SPLIT, true>(dacc, acc, near_ld<SM>(kub + idx), *(hqb - h));
-            if (HW) near_fma<SPLIT, false>(dacc, acc, near_ld<SM>(kwb + idx), *(hub - h));
+            if (HU) near_fma<SPLIT, true>(dacc, acc, __ldcs(kub + idx), *(hqb - h));
+            if (HW) near_fma<SPLIT, false>(dacc, acc, __ldcs(kwb + idx), *(hub - h));
         }
         pos += __popc(mask);
     }
 }
 
-template <bool HU, bool HW, bool SPLIT, bool SM>
+template <bool HU, bool HW, bool SPLIT>
 __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__restrict__ kub,
                                            const typename NearV<SPLIT>::T *__restrict__ kwb,
                                            const typename NearV<SPLIT>::T *__restrict__ hqb,
@@ -208,7 +196,7 @@ __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__res
     const int nf = cmin < MF ? cmin : MF;
 #define TDBEM_NEAR_CASE(n)                                                                                     \
     case n:                                                                                                    \
-        if constexpr (n <= MF) near_slots<HU, HW, SPLIT, n, SM>(kub, kwb, hqb, hub, ns, lane, lt, cnt, tail, dacc, acc); \
+        if constexpr (n <= MF) near_slots<HU, HW, SPLIT, n>(kub, kwb, hqb, hub, ns, lane, lt, cnt, tail, dacc, acc); \
         break;
     switch (nf) {  // warp-uniform
         TDBEM_NEAR_CASE(0)
@@ -223,7 +211,7 @@ __device__ __forceinline__ void near_block(const typename NearV<SPLIT>::T *__res
     // slots the unrolled bodies did not reach
     const int done = nf + (tail ? 1 : 0);
     if (done < cmax)
-        near_slots_rest<HU, HW, SPLIT, SM>(kub, kwb, hqb, hub, ns, lane, lt, cnt, done, cmin, cmax, dacc, acc);
+        near_slots_rest<HU, HW, SPLIT>(kub, kwb, hqb, hub, ns, lane, lt, cnt, done, cmin, cmax, dacc, acc);
 }
 
 // Asks L2 to fetch the coefficient bytes [a, e) of a block ahead of its
@@ -237,87 +225,14 @@ __device__ __forceinline__ void near_prefetch(const double *k, int64_t a, int64_
     if (p < end) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Staged coefficient loads (ST > 0): each warp keeps a ring of ST stages in
-// shared memory; one lane brings a block's coefficients (both kinds if the
-// run has both) into a stage with bulk copies (cp.async.bulk, completion on
-// the stage's mbarrier), ST blocks ahead of the one being summed, so ST
-// blocks per warp are in flight without registers.  Bulk copies move whole
-// 16-byte units: the copied range is the block's range widened to 16-byte
-// boundaries (the coefficient arrays carry 16 bytes of slack at the end) and
-// the warp reads from the block's offset within it.  Every wait is bounded
-// (kStageWaitNs of global time; then the error flags get the value 16, the block is
-// skipped and the outstanding copies are waited for before the warp ends).
-constexpr unsigned long long kStageWaitNs = 2000000000ull;
-
-__device__ __forceinline__ unsigned long long near_clock()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool stage_test(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity)
-{
-    if (stage_test(bar, parity)) return true;
-    const unsigned long long t0 = near_clock();
-    while (!stage_test(bar, parity))
-        if (near_clock() - t0 > kStageWaitNs) return false;
-    return true;
-}
-
-// Lane 0: one stage's bulk copies of the block's coefficient range [a, e)
-// (8-byte units) of up to two streams.
-__device__ __forceinline__ void stage_issue(uint32_t bar, uint32_t dst_u, uint32_t dst_w, const double *ku,
-                                            const double *kw, int64_t a, int64_t e)
-{
-    uint32_t bytes = 0, nu = 0, nw = 0;
-    size_t su = 0, sw = 0;
-    if (ku) {
-        su = __cvta_generic_to_global(ku + a) & ~(size_t)15;
-        nu = (uint32_t)(((__cvta_generic_to_global(ku + e) + 15) & ~(size_t)15) - su);
-        if (e <= a) nu = 0;
-        bytes += nu;
-    }
-    if (kw) {
-        sw = __cvta_generic_to_global(kw + a) & ~(size_t)15;
-        nw = (uint32_t)(((__cvta_generic_to_global(kw + e) + 15) & ~(size_t)15) - sw);
-        if (e <= a) nw = 0;
-        bytes += nw;
-    }
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    if (nu)
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         dst_u),
-                     "l"(su), "r"(nu), "r"(bar)
-                     : "memory");
-    if (nw)
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         dst_w),
-                     "l"(sw), "r"(nw), "r"(bar)
-                     : "memory");
-}
-
-template <bool HU, bool HW, bool SPLIT, int WPR, bool COL, int ST>
+template <bool HU, bool HW, bool SPLIT, int WPR, bool COL>
 __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const int64_t *__restrict__ prow,
                                          const int32_t *__restrict__ crow, const int64_t *__restrict__ rowblk,
                                          const uint16_t *__restrict__ meta, const int64_t *__restrict__ boff,
                                          const double *__restrict__ ku, const double *__restrict__ kw,
                                          const double *__restrict__ u_, const double *__restrict__ q,
                                          const float2 *__restrict__ us, const float2 *__restrict__ qs, DF &dacc,
-                                         double &acc, uint8_t *stg, int stage_bytes, int *flag)
+                                         double &acc)
 {
     using V = typename NearV<SPLIT>::T;
     constexpr int W = WPR;  // the row's warps take its blocks in turn
@@ -338,37 +253,13 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
     const int nblk = (int)(rowblk[i + 1] - rowblk[i]);
     const V *kuv = reinterpret_cast<const V *>(ku);
     const V *kwv = reinterpret_cast<const V *>(kw);
-    // staged: the warp's ring of ST stages (stage t: [kind u | kind w], each
-    // stage_bytes) and its ST mbarriers after the rings of all warps
-    uint32_t bar0 = 0, ring0 = 0;
-    if constexpr (ST > 0) {
-        const int wid = threadIdx.x >> 5;
-        const int kinds = (HU ? 1 : 0) + (HW ? 1 : 0);
-        ring0 = (uint32_t)__cvta_generic_to_shared(stg + (size_t)wid * ST * kinds * stage_bytes);
-        bar0 = (uint32_t)__cvta_generic_to_shared(stg + (size_t)kNearWarps * ST * kinds * stage_bytes) + 8u * ST * wid;
-        if (lane == 0) {
-            for (int t = 0; t < ST; ++t)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * t), "r"(1u) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            for (int t = 0; t < ST; ++t) {
-                const int pb = wr + W * t;
-                if (pb < nblk) {
-                    const uint32_t st0 = ring0 + (uint32_t)(t * kinds * stage_bytes);
-                    stage_issue(bar0 + 8u * t, st0, st0 + (HU ? (uint32_t)stage_bytes : 0u), HU ? ku : nullptr,
-                                HW ? kw : nullptr, orow[pb], orow[pb + 1]);
-                }
-            }
-        }
-        __syncwarp();
-    } else {
-        // the warp asks L2 for the coefficients of its block kNearPrefetch
-        // blocks ahead (here: of its first kNearPrefetch blocks)
-        for (int t = 0; t < kNearPrefetch; ++t) {
-            const int pb = wr + W * t;
-            if (pb < nblk) {
-                if (HU) near_prefetch(ku, orow[pb], orow[pb + 1], lane);
-                if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
-            }
+    // the warp asks L2 for the coefficients of its block kNearPrefetch blocks
+    // ahead (here: of its first kNearPrefetch blocks)
+    for (int t = 0; t < kNearPrefetch; ++t) {
+        const int pb = wr + W * t;
+        if (pb < nblk) {
+            if (HU) near_prefetch(ku, orow[pb], orow[pb + 1], lane);
+            if (HW) near_prefetch(kw, orow[pb], orow[pb + 1], lane);
         }
     }
     // metadata and columns of the first block; the next block's are fetched
@@ -383,10 +274,8 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
         if constexpr (COL) jnext = (pr < npr) ? crow[pr] : 0;
         onext = orow[bk];
     }
-    int it = 0;    // blocks of this warp so far
-    bool ok = true;
-    for (; bk < nblk; bk += W, ++it) {
-        if constexpr (ST == 0) {
+    for (; bk < nblk; bk += W) {
+        {
             const int pb = bk + W * kNearPrefetch;
             if (pb < nblk) {
                 if (HU) near_prefetch(ku, orow[pb], orow[pb + 1], lane);
@@ -407,44 +296,8 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
         // beta = alpha - g0 - s
         const int g0 = (int)(m & kMaxG0), cnt = (int)(m >> kG0Bits);
         const int64_t hb = (int64_t)(alpha - g0) * ns + j;
-        if constexpr (ST > 0) {
-            const int t = it % ST;
-            const int kinds = (HU ? 1 : 0) + (HW ? 1 : 0);
-            uint8_t *sbase = stg + ((size_t)(threadIdx.x >> 5) * ST + t) * kinds * stage_bytes;
-            ok = __all_sync(0xffffffffu, ok && stage_wait(bar0 + 8u * t, (uint32_t)((it / ST) & 1)));
-            if (!ok) {
-                if (lane == 0) atomicOr(flag, 16);
-                break;
-            }
-            // the block's coefficients start (o mod 2) 8-byte units into the stage
-            const int sh = (int)((__cvta_generic_to_global(kuv + o) >> 3) & 1);
-            const int shw = (int)((__cvta_generic_to_global(kwv + o) >> 3) & 1);
-            const V *su = reinterpret_cast<const V *>(sbase) + sh;
-            const V *sw = reinterpret_cast<const V *>(sbase + (HU ? stage_bytes : 0)) + shw;
-            near_block<HU, HW, SPLIT, true>(su, sw, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
-            // every lane has its values: the stage takes the block ST ahead
-            __syncwarp();
-            const int pb = bk + W * ST;
-            if (lane == 0 && pb < nblk) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const uint32_t st0 = ring0 + (uint32_t)(t * kinds * stage_bytes);
-                stage_issue(bar0 + 8u * t, st0, st0 + (HU ? (uint32_t)stage_bytes : 0u), HU ? ku : nullptr,
-                            HW ? kw : nullptr, orow[pb], orow[pb + 1]);
-            }
-        } else {
-            near_block<HU, HW, SPLIT, false>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
-        }
+        near_block<HU, HW, SPLIT>(kuv + o, kwv + o, hq + hb, hu + hb, cnt, ns, lane, lt, dacc, acc);
         if (SPLIT) df_renorm(dacc);
-    }
-    if constexpr (ST > 0) {
-        // after a wait that gave up, the copies still in flight land before
-        // the warp ends
-        if (!ok && lane == 0)
-            for (int t2 = 0; t2 < ST; ++t2) {
-                const int i2 = it + t2;
-                if (wr + W * i2 < nblk) stage_wait(bar0 + 8u * (i2 % ST), (uint32_t)((i2 / ST) & 1));
-            }
-        __syncwarp();
     }
 }
 
@@ -462,7 +315,7 @@ __device__ __forceinline__ void near_row(int i, int wr, int ns, int alpha, const
 // SPLIT = false: FP64 coefficients and FP64 FMA.  SPLIT = true: each
 // coefficient is a float pair (hi, lo) in the same 8 bytes, the histories
 // are read from their float-pair copies and the sum runs in double-float.
-template <bool HU, bool HW, bool SPLIT, int WPR, bool COL, int ST>
+template <bool HU, bool HW, bool SPLIT, int WPR, bool COL>
 __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_near_sum(int ns, int alpha, const int *__restrict__ alpha_dev,
                                                               const int64_t *__restrict__ prow,
                                                               const int32_t *__restrict__ col,
@@ -482,9 +335,8 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
                                                               const double *__restrict__ xc,
                                                               const double *__restrict__ nrm,
                                                               const double *__restrict__ far, int far_lt, int alim,
-                                                              double *b, int stage_bytes, int *flag)
+                                                              double *b)
 {
-    extern __shared__ __align__(16) uint8_t near_stg[];
     __shared__ double red[kNearWarps];
     if (alpha_dev) {
         // graph-replayed steps: an instance past its last step (alim = Nt-1)
@@ -500,8 +352,8 @@ __global__ void __launch_bounds__(kNearThreads, SPLIT ? kNearMinBlocks : 8) k_ne
     DF dacc = {0.f, 0.f};
     if (i < ns) {
         const int32_t *crow = COL ? col + coff[e2c[i]] : nullptr;
-        near_row<HU, HW, SPLIT, WPR, COL, ST>(i, wr, ns, alpha, prow, crow, rowblk, meta, boff, ku, kw, u_, q, us,
-                                              qs, dacc, acc, near_stg, stage_bytes, flag);
+        near_row<HU, HW, SPLIT, WPR, COL>(i, wr, ns, alpha, prow, crow, rowblk, meta, boff, ku, kw, u_, q, us, qs,
+                                          dacc, acc);
     }
     if (SPLIT) acc = (double)dacc.h + (double)dacc.l;
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -526,27 +378,17 @@ template <bool SPLIT, int WPR, bool COL>
 static cudaError_t near_dispatch(tdbem_ctx *c, int alpha, const double *d_exc, const double *d_far)
 {
     bool hu = c->d_ku != nullptr, hw = c->d_kw != nullptr;
-    // the split form stages its coefficient blocks in shared memory
-    constexpr int ST = SPLIT ? kNearStages : 0;
-    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, WPR, COL, ST> : k_near_sum<true, false, SPLIT, WPR, COL, ST>)
-                : (hw ? k_near_sum<false, true, SPLIT, WPR, COL, ST> : k_near_sum<false, false, SPLIT, WPR, COL, ST>);
+    auto k = hu ? (hw ? k_near_sum<true, true, SPLIT, WPR, COL> : k_near_sum<true, false, SPLIT, WPR, COL>)
+                : (hw ? k_near_sum<false, true, SPLIT, WPR, COL> : k_near_sum<false, false, SPLIT, WPR, COL>);
     constexpr int rows = kNearWarps / WPR;
-    const int stage_bytes = ST ? ((32 * std::min(c->smax, kMaxCnt) * 8 + 15) / 16 * 16 + 16) : 0;
-    const int kinds = (hu ? 1 : 0) + (hw ? 1 : 0);
-    const size_t shm = ST ? (size_t)kNearWarps * ST * (kinds * stage_bytes + 8) : 0;
-    if (shm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        if (e != cudaSuccess) return e;
-    }
     // the kernel uses a pair's column only to address the history: in the
     // split form with near lists that is the column's sorted position
     const int32_t *hcol = COL ? ((SPLIT && c->d_chcol) ? c->d_chcol : c->d_ccol) : nullptr;
-    k<<<(c->ns + rows - 1) / rows, kNearThreads, shm, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, hcol,
+    k<<<(c->ns + rows - 1) / rows, kNearThreads, 0, c->s>>>(c->ns, alpha, c->alpha_dev_on ? c->d_alpha : nullptr, c->d_prow, hcol,
                                        COL ? c->d_coff : nullptr, COL ? c->tree.e2c : nullptr,
                                        COL ? c->tree.perm : nullptr, c->d_rowblk, c->d_meta, c->d_boff,
                                        c->d_ku, c->d_kw, c->d_u, c->d_q, c->d_us, c->d_qs, d_exc, c->inc, c->d_xc,
-                                       c->d_n, d_far, c->alpha_dev_on && d_far ? c->fmm.Lt : 0, c->P.nt - 1, c->d_b,
-                                       stage_bytes, c->d_flag);
+                                       c->d_n, d_far, c->alpha_dev_on && d_far ? c->fmm.Lt : 0, c->P.nt - 1, c->d_b);
     return cudaGetLastError();
 }
 
