@@ -296,7 +296,9 @@ def run_fmm(args):
     if prec and abi.tdbem_steps_done(ctx) + nsteps <= w.nt - 1:
         abi.tdbem_set_overlap(ctx, 0)
         abi.tdbem_reset_stats(ctx)
+        torch.cuda.nvtx.range_push("alone")
         ms_alone = _timed(abi, torch, ctx, nsteps) / nsteps
+        torch.cuda.nvtx.range_pop()
         st_alone = s.stats()
         abi.tdbem_set_overlap(ctx, 1)
     out = {
