@@ -1,8 +1,10 @@
 """Plain definitions of the space-time FMM pieces (oracle, TEST
 INFRASTRUCTURE ONLY).
 
-So far: the coefficients c_m^p(k) of the O(Nt) M2L recurrence (Formula 1,
-Eq. cmp) and n_d, the number of auxiliary local coefficients (Remark aux).
+The coefficients c_m^p(k) of the O(Nt) M2L recurrence (Formula 1, Eq. cmp)
+and n_d, the number of auxiliary local coefficients (Remark aux); the
+space-time hierarchy, P2M, the M2L of Eq. m2l_actual (plain, and through
+the FFT with equispaced nodes) and L2P.
 """
 
 from math import comb
@@ -51,6 +53,13 @@ def cheb(p):
     return np.cos((2.0 * np.arange(p) + 1.0) * np.pi / (2.0 * p))
 
 
+def equi(p):
+    """p equispaced points on [-1, 1], the ends included (0 for p = 1): the
+    nodes of the FFT form of the M2L (Section 4, the estimate after
+    Algorithm 1), under which every M2L block is a Toeplitz matrix."""
+    return np.linspace(-1.0, 1.0, p) if p > 1 else np.zeros(1)
+
+
 def lagrange(nodes, xi):
     """Values and derivatives of the Lagrange basis of ``nodes`` at xi."""
     p = len(nodes)
@@ -69,7 +78,7 @@ def lagrange(nodes, xi):
 class Hierarchy:
     """Parameters of the space-time hierarchy of one mesh (see above)."""
 
-    def __init__(self, xyz, tri, L, c, dt, nt, ps, pt, d, mu=0):
+    def __init__(self, xyz, tri, L, c, dt, nt, ps, pt, d, mu=0, nodes="cheb"):
         from . import coeffs as oc
         from . import tree as ot
         v, xc, n, _ = oc.geometry(xyz, tri)
@@ -83,7 +92,10 @@ class Hierarchy:
         cdt = c * dt
         self.s = [self.side / (1 << l) for l in range(L + 1)]
         self.hs = [self.s[l] / 2.0 + self.rho for l in range(L + 1)]
-        self.ho = [self.s[l] / 2.0 for l in range(L + 1)]
+        self.nodes = nodes
+        # FFT form: equispaced nodes, and the observation box is the source
+        # box, so that node differences depend only on index differences
+        self.ho = list(self.hs) if nodes == "equi" else [self.s[l] / 2.0 for l in range(L + 1)]
         self.Lt = int(np.floor((self.s[L] - self.rho) / cdt))
         if self.Lt < 1 or not (2.0 * self.rho < self.s[L]):
             raise ValueError("infeasible hierarchy: leaf cells too small for c dt and the element size")
@@ -93,7 +105,7 @@ class Hierarchy:
             rmax = np.sqrt(3.0) * (3.0 * self.s[l] + self.hs[l] + self.ho[l])
             m = max(m, int(np.floor((rmax / cdt - 1.0) / self.Tl[l])) + 1)
         self.mu = max(m, mu)
-        self.ws, self.wt = cheb(ps), cheb(pt)
+        self.ws, self.wt = (equi(ps), equi(pt)) if nodes == "equi" else (cheb(ps), cheb(pt))
         # cell index of every element at every level
         self.cell = []
         for l in range(L + 1):
@@ -265,6 +277,57 @@ def m2l_naive(H, l, Ms, O, k):
     return Lloc
 
 
+def _circulant_axis(p, N):
+    """Index differences D = a - b (|D| <= p - 1) at their circular positions
+    D mod N of an N-point axis (N >= 2p - 1); other positions stay 0."""
+    D = np.zeros(N)
+    on = np.zeros(N, dtype=bool)
+    for t in range(-(p - 1), p):
+        D[t % N] = t
+        on[t % N] = True
+    return D, on
+
+
+def m2l_fft(H, l, Ms, O, k):
+    """The same sum as m2l_naive, each block U(O, S, I_k, J_k') applied by the
+    FFT (Section 4, the complexity estimate after Algorithm 1).  With
+    equispaced nodes and equal boxes, x_a - y_b = c_O - c_S + h (w_a - w_b)
+    and t_m - s_n = c_I - c_J + h_t (w_m - w_n) depend only on a - b and
+    m - n, so a block is a four-level Toeplitz matrix.  Embedded in a
+    circulant of 2 p_s points per spatial axis and 2 p_t in time, it acts
+    as a circular convolution: U M = IFFT(FFT(u) FFT(M padded)) restricted
+    to the first p_s^3 x p_t entries.  Returns [P_s, P_t]."""
+    if H.nodes != "equi":
+        raise ValueError("the FFT form needs equispaced nodes")
+    ps, pt = H.ps, H.pt
+    Ns, Nt = 2 * ps, 2 * pt
+    hsp = H.hs[l] * (2.0 / (ps - 1) if ps > 1 else 0.0)
+    Ds, ons = _circulant_axis(ps, Ns)
+    Dt, ont = _circulant_axis(pt, Nt)
+    ci, hi = H.obs_interval(l, k)
+    co = H.centre(l, O)
+    Y = np.zeros((Nt, Ns, Ns, Ns), dtype=complex)
+    for S in H.T["il"][l][O]:
+        dc = co - H.centre(l, S)
+        # axes (t, z, y, x): the vector index b1 + p (b2 + p b3) + P3 n
+        rx = dc[0] + hsp * Ds[None, None, None, :]
+        ry = dc[1] + hsp * Ds[None, None, :, None]
+        rz = dc[2] + hsp * Ds[None, :, None, None]
+        r = np.sqrt(rx * rx + ry * ry + rz * rz)
+        mask = ons[None, None, None, :] & ons[None, None, :, None] & ons[None, :, None, None]
+        for kp in range(k):
+            cj, hj = H.src_interval(l, kp)
+            htp = hj * (2.0 / (pt - 1) if pt > 1 else 0.0)
+            tau = (ci - cj) + htp * Dt
+            z = H.c * tau[:, None, None, None] - r
+            u = np.where((z > 0) & mask & ont[:, None, None, None], np.maximum(z, 0.0) ** H.d, 0.0) / r
+            X = np.zeros((Nt, Ns, Ns, Ns))
+            X[:pt, :ps, :ps, :ps] = Ms[kp][S].T.reshape(pt, ps, ps, ps)
+            Y += np.fft.fftn(u) * np.fft.fftn(X)
+    y = np.fft.ifftn(Y).real[:pt, :ps, :ps, :ps]
+    return y.reshape(pt, ps ** 3).T.copy()
+
+
 def l2p(H, l, O, Lloc, i, alpha, bie):
     """Psi(x_i, t_alpha) = sum_{a,m} D_a ell_m(t_alpha) L_{a,m} (Eq. target_m2l);
     BMBIE applies (d/dn_x - c^-1 d/dt) to ell_a ell_m (Section 3)."""
@@ -277,11 +340,13 @@ def l2p(H, l, O, Lloc, i, alpha, bie):
     return float(dn @ Lloc @ lt - val @ Lloc @ (dlt / hi) / H.c)
 
 
-def far_field(H, u, q, alphas, bie, rows=None):
+def far_field(H, u, q, alphas, bie, rows=None, m2l=None):
     """The interpolated far field Psi(x_i, t_alpha) of every row for the given
     steps: sum over levels l >= 2 of L2P of the naive M2L of the directly
     computed moments of the interaction-list cells (every past interval).
-    u, q: B-spline coefficient histories [>= max(alphas), ns]."""
+    u, q: B-spline coefficient histories [>= max(alphas), ns].  m2l: the
+    M2L route (m2l_naive, or m2l_fft with equispaced nodes)."""
+    m2l = m2l or m2l_naive
     ns = H.xc.shape[0]
     rows = range(ns) if rows is None else rows
     tau = fold(q, H.d)
@@ -297,6 +362,6 @@ def far_field(H, u, q, alphas, bie, rows=None):
             for ri, i in enumerate(rows):
                 O = H.cell[l][i]
                 if (O, k) not in cache:
-                    cache[(O, k)] = m2l_naive(H, l, Ms, O, k)
+                    cache[(O, k)] = m2l(H, l, Ms, O, k)
                 out[ai, ri] += l2p(H, l, O, cache[(O, k)], i, a, bie)
     return out
