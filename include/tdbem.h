@@ -70,7 +70,7 @@ typedef struct {
     int32_t algo;         /* 0 = direct history sum over all element pairs (Eq. linear);
                              1 = near pairs (leaf neighbours) direct + the far part by the
                              interpolation-based space-time FMM (Sections 3-4, Formula 1) */
-    int32_t precision;    /* 0 = FP64 throughout; 1..4 = split: the history sum stores every
+    int32_t precision;    /* 0 = FP64 throughout; 1..5 = split: the history sum stores every
                              coefficient and history value as an FP32 pair (hi, lo) (48
                              significant bits) and sums in double-float arithmetic on the
                              FP32 pipes; coefficients, the zero-lag matrix and the solve
@@ -80,7 +80,12 @@ typedef struct {
                              terms, six products (FP32-grade); 2 = BF16x3 (two terms,
                              three products); 3 = one BF16 product; 4 = two FP16 terms
                              scaled by powers of two per operator row and per cell's
-                             moment, three products (about 22 bits).  The last near-future
+                             moment, three products (about 22 bits); 5 = the near-future
+                             blocks by the FFT (Section 4, the estimate after Algorithm 1):
+                             equispaced nodes, the observation box equal to the source
+                             box, so each block is a Toeplitz matrix applied as a circular
+                             convolution on a 2ps x 2ps x 2ps x 2pt grid, FP32 transforms
+                             and products on the CUDA cores.  The last near-future
                              block, the derivative rows and the recurrence of Formula 1
                              stay FP64 / double-float in every form. */
     int32_t ps, pt;       /* FMM: interpolation points per space / time dimension (2..8,
@@ -209,7 +214,7 @@ int tdbem_step_io(tdbem_ctx *ctx, int32_t nsteps, const double *exc, double *x_o
 int tdbem_step_graph(tdbem_ctx *ctx, int32_t nsteps);
 
 /* Batched driver: several independent instances (contexts on one device,
- * direct path or FMM in a tensor-core precision, e.g. scatterers of
+ * direct path or FMM in a precision from 1 to 5, e.g. scatterers of
  * different size, order and BIE)
  * advanced together, each step of all of them one replay of a single CUDA
  * graph in which every instance's step is an independent branch, so that

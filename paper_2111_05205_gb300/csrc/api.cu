@@ -150,7 +150,7 @@ int tdbem_create(const tdbem_params *p, void *stream, tdbem_ctx **out)
     if (!p || !out) return TDBEM_ERR_ARG;
     *out = nullptr;
     if (!(p->c > 0) || !(p->dt > 0) || p->nt < 2 || p->d < 1 || p->d > kMaxD || (p->bie != 0 && p->bie != 1) ||
-        (p->algo != 0 && p->algo != 1) || p->precision < 0 || p->precision > 4 || (p->precond != 0 && p->precond != 1))
+        (p->algo != 0 && p->algo != 1) || p->precision < 0 || p->precision > 5 || (p->precond != 0 && p->precond != 1))
         return TDBEM_ERR_ARG;
     c = new tdbem_ctx();
     c->P = *p;
@@ -562,7 +562,7 @@ static int graph_ready(tdbem_ctx *c)
 {
     if (!c->prepared) return fail(c, TDBEM_ERR_STATE, "graph step before prepare");
     if (c->fmm.on && !c->split)
-        return fail(c, TDBEM_ERR_ARG, "graph-replayed FMM steps need a tensor-core precision (1-4)");
+        return fail(c, TDBEM_ERR_ARG, "graph-replayed FMM steps need a precision from 1 to 5 (not the FP64 form)");
     if (c->sai_val) return fail(c, TDBEM_ERR_ARG, "graph-replayed steps use the Jacobi zero-lag solve");
     if (!c->d_alpha) TD_CUDA(dalloc(c, &c->d_alpha, 1));
     TD_CUDA(fmm_join(c));

@@ -36,13 +36,19 @@ namespace tdbem {
 
 constexpr int kMaxP = 8;
 
-__device__ __forceinline__ double cheb_node(int p, int a) { return cos((2.0 * a + 1.0) * 3.14159265358979323846 / (2.0 * p)); }
+// Interpolation node a of p on [-1, 1]: Chebyshev points of the first kind,
+// or (eq, the FFT form) p equispaced points with both ends.
+__device__ __forceinline__ double fmm_node(int p, int a, bool eq)
+{
+    if (eq) return p > 1 ? -1.0 + 2.0 * a / (p - 1) : 0.0;
+    return cos((2.0 * a + 1.0) * 3.14159265358979323846 / (2.0 * p));
+}
 
-// Lagrange basis of the p Chebyshev nodes at xi (values and derivatives).
-__device__ void lag_basis(int p, double xi, double *val, double *der)
+// Lagrange basis of the p nodes at xi (values and derivatives).
+__device__ void lag_basis(int p, double xi, double *val, double *der, bool eq)
 {
     double w[kMaxP];
-    for (int a = 0; a < p; ++a) w[a] = cheb_node(p, a);
+    for (int a = 0; a < p; ++a) w[a] = fmm_node(p, a, eq);
     for (int a = 0; a < p; ++a) {
         double v = 1.0, dv = 0.0;
         for (int b = 0; b < p; ++b) {
@@ -91,7 +97,7 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
                                   const double *__restrict__ xyz, const int32_t *__restrict__ tri,
                                   const double *__restrict__ xc, const double *__restrict__ nrm,
                                   const uint64_t *__restrict__ key, int nq, const double *__restrict__ qx,
-                                  const double *__restrict__ qw, double *At, double *As, double *Dv, double *Dn)
+                                  const double *__restrict__ qw, double *At, double *As, double *Dv, double *Dn, bool eq)
 {
     int j = blockIdx.x;
     if (j >= ns) return;
@@ -114,7 +120,7 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
             double y[3];
             for (int k = 0; k < 3; ++k) y[k] = v[k] + u * e1[k] + t * e2[k];
             double l[3][kMaxP], dl[3][kMaxP];
-            for (int k = 0; k < 3; ++k) lag_basis(ps, (y[k] - cen[k]) / hs, l[k], dl[k]);
+            for (int k = 0; k < 3; ++k) lag_basis(ps, (y[k] - cen[k]) / hs, l[k], dl[k], eq);
             double val = l[0][b1] * l[1][b2] * l[2][b3];
             double g0 = dl[0][b1] * l[1][b2] * l[2][b3] / hs, g1 = l[0][b1] * dl[1][b2] * l[2][b3] / hs,
                    g2 = l[0][b1] * l[1][b2] * dl[2][b3] / hs;
@@ -125,7 +131,7 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
         As[(int64_t)j * P3 + b] = as;
         // L2P values at the collocation point of element j (observation box)
         double l[3][kMaxP], dl[3][kMaxP];
-        for (int k = 0; k < 3; ++k) lag_basis(ps, (xc[3 * j + k] - cen[k]) / ho, l[k], dl[k]);
+        for (int k = 0; k < 3; ++k) lag_basis(ps, (xc[3 * j + k] - cen[k]) / ho, l[k], dl[k], eq);
         Dv[(int64_t)j * P3 + b] = l[0][b1] * l[1][b2] * l[2][b3];
         Dn[(int64_t)j * P3 + b] = (dl[0][b1] * l[1][b2] * l[2][b3] * n[0] + l[0][b1] * dl[1][b2] * l[2][b3] * n[1] +
                                   l[0][b1] * l[1][b2] * dl[2][b3] * n[2]) / ho;
@@ -143,7 +149,7 @@ __global__ void k_element_weights(int ns, int ps, int L, const double *__restric
 //   U^(p) = C(d, p) (c (t_m - s_n) - r)_+^(d-p) / r,
 // x_a - y_b = -offset s + ho w_a - hs w_b, t_m - s_n = l T dt + dt + ht (w_m - w_n).
 __global__ void k_m2l_operators(int ps, int pt, int d, int mu, int nblk, double s, double hs, double ho, double T_dt, double dt,
-                                double ht, double c, int noff, const int32_t *__restrict__ offs, double *op)
+                                double ht, double c, int noff, const int32_t *__restrict__ offs, double *op, bool eq)
 {
     const int P3 = ps * ps * ps, P = P3 * pt;
     int64_t total = (int64_t)noff * nblk * P * P;
@@ -163,13 +169,13 @@ __global__ void k_m2l_operators(int ps, int pt, int d, int mu, int nblk, double 
         int a = row % P3, m = row / P3, b = col % P3, n = col / P3;
         int a1 = a % ps, a2 = (a / ps) % ps, a3 = a / (ps * ps);
         int b1 = b % ps, b2 = (b / ps) % ps, b3 = b / (ps * ps);
-        double rx = -dx * s + ho * cheb_node(ps, a1) - hs * cheb_node(ps, b1);
-        double ry = -dy * s + ho * cheb_node(ps, a2) - hs * cheb_node(ps, b2);
-        double rz = -dz * s + ho * cheb_node(ps, a3) - hs * cheb_node(ps, b3);
+        double rx = -dx * s + ho * fmm_node(ps, a1, eq) - hs * fmm_node(ps, b1, eq);
+        double ry = -dy * s + ho * fmm_node(ps, a2, eq) - hs * fmm_node(ps, b2, eq);
+        double rz = -dz * s + ho * fmm_node(ps, a3, eq) - hs * fmm_node(ps, b3, eq);
         double r = sqrt(rx * rx + ry * ry + rz * rz);
         int l = (blk <= mu) ? blk + 1 : mu + 1;
         int pw = (blk <= mu) ? 0 : blk - mu;
-        double tdiff = l * T_dt + dt + ht * (cheb_node(pt, m) - cheb_node(pt, n));
+        double tdiff = l * T_dt + dt + ht * (fmm_node(pt, m, eq) - fmm_node(pt, n, eq));
         double z = c * tdiff - r;
         double v = 0.0;
         if (z > 0.0) {
@@ -732,7 +738,7 @@ static int reduce_rows(int P3, int R)
 // slot e = 1, r^0 = 1, is not read), r_ab = |-c s + ho w_a - hs w_b|.
 template <typename T>
 __global__ void k_dist_powers(int ncls, int ps, int d, double s, double hs, double ho, const int32_t *__restrict__ codes,
-                              T *out)
+                              T *out, bool eq)
 {
     const int P3 = ps * ps * ps;
     const int64_t n = (int64_t)ncls * (d + 1) * P3 * P3;
@@ -743,9 +749,9 @@ __global__ void k_dist_powers(int ncls, int ps, int d, double s, double hs, doub
         const int dx = o % 7 - 3, dy = (o / 7) % 7 - 3, dz = o / 49 - 3;
         const int a1 = a % ps, a2 = (a / ps) % ps, a3 = a / (ps * ps);
         const int b1 = b % ps, b2 = (b / ps) % ps, b3 = b / (ps * ps);
-        const double rx = -dx * s + ho * cheb_node(ps, a1) - hs * cheb_node(ps, b1);
-        const double ry = -dy * s + ho * cheb_node(ps, a2) - hs * cheb_node(ps, b2);
-        const double rz = -dz * s + ho * cheb_node(ps, a3) - hs * cheb_node(ps, b3);
+        const double rx = -dx * s + ho * fmm_node(ps, a1, eq) - hs * fmm_node(ps, b1, eq);
+        const double ry = -dy * s + ho * fmm_node(ps, a2, eq) - hs * fmm_node(ps, b2, eq);
+        const double rz = -dz * s + ho * fmm_node(ps, a3, eq) - hs * fmm_node(ps, b3, eq);
         const double r = sqrt(rx * rx + ry * ry + rz * rz);
         double v = 1.0 / r;
         for (int k = 0; k < ex; ++k) v *= r;
@@ -1116,16 +1122,20 @@ __global__ void k_zero_when(int64_t n, double *x, StepWhen w)
 
 namespace {
 
-double h_cheb(int p, int a) { return cos((2.0 * a + 1.0) * M_PI / (2.0 * p)); }
+double h_node(int p, int a, bool eq)
+{
+    if (eq) return p > 1 ? -1.0 + 2.0 * a / (p - 1) : 0.0;
+    return cos((2.0 * a + 1.0) * M_PI / (2.0 * p));
+}
 
-void h_lagrange(int p, double xi, double *val, double *der)
+void h_lagrange(int p, double xi, double *val, double *der, bool eq)
 {
     for (int a = 0; a < p; ++a) {
         double v = 1.0, dv = 0.0;
         for (int b = 0; b < p; ++b) {
             if (b == a) continue;
-            double den = h_cheb(p, a) - h_cheb(p, b);
-            double f = (xi - h_cheb(p, b)) / den;
+            double den = h_node(p, a, eq) - h_node(p, b, eq);
+            double f = (xi - h_node(p, b, eq)) / den;
             dv = dv * f + v / den;
             v *= f;
         }
@@ -1311,7 +1321,7 @@ static cudaError_t m2l_products(tdbem_ctx *c, FmmLevel &V, StepWhen w = StepWhen
 // sum_b r_ab^(e-1) sum_n w_n^j M[b,n] and
 // coef = C(d,p) sum_{i+j+k=q, k>=e} C(q,i) C(q-i,j) (cht w_m)^i (-cht)^j C(k,e) A^(k-e) (-1)^e
 // (layout [d+1][pt][d+1][d+1]).
-static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht)
+static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht, bool eq)
 {
     auto binom = [](int n, int k) {
         double v = 1.0;
@@ -1323,7 +1333,7 @@ static std::vector<double> deriv_coef_table(int d, int pt, double A, double cht)
     for (int p = 0; p <= d; ++p) {
         const int q = d - p;
         for (int m = 0; m < pt; ++m) {
-            const double wm = h_cheb(pt, m);
+            const double wm = h_node(pt, m, eq);
             for (int i = 0; i <= q; ++i)
                 for (int j = 0; i + j <= q; ++j) {
                     const int k = q - i - j;
@@ -1408,6 +1418,12 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     }
     F.P3 = F.ps * F.ps * F.ps;
     F.P = F.P3 * F.pt;
+    // precision 5: near-future M2L blocks by the FFT, on equispaced nodes
+    // with the observation box equal to the source box (Toeplitz blocks)
+    F.fft = c->P.precision == 5;
+    F.fNs = 2 * F.ps;
+    F.fNt = 2 * F.pt;
+    F.fN = (int64_t)F.fNs * F.fNs * F.fNs * F.fNt;
     if (F.P > 4096) {
         why = "FMM needs ps^3 pt <= 4096";
         return cudaSuccess;
@@ -1435,7 +1451,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     for (int l = 0; l <= L; ++l) {
         F.lev[l].s = box[3] / (double)(1 << l);
         F.lev[l].hs = F.lev[l].s / 2.0 + F.rho;
-        F.lev[l].ho = F.lev[l].s / 2.0;
+        F.lev[l].ho = F.fft ? F.lev[l].hs : F.lev[l].s / 2.0;
     }
     F.Lt = (int)floor((F.lev[L].s - F.rho) / cdt);
     if (F.Lt < 1 || !(2.0 * F.rho < F.lev[L].s)) {
@@ -1484,7 +1500,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         // products (A term, B term) kept: all with s + t < nterm
         // (precision 4: two FP16 terms with power-of-two scales, products
         // (0,0), (0,1), (1,0))
-        const int nterm = c->P.precision == 1 ? 3 : (c->P.precision == 2 || c->P.precision == 4) ? 2 : 1;
+        const int nterm = F.fft ? 0 : c->P.precision == 1 ? 3 : (c->P.precision == 2 || c->P.precision == 4) ? 2 : 1;
         F.nta = F.ntb = nterm;
         F.f16 = c->P.precision == 4;
         F.nprod = 0;
@@ -1521,7 +1537,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     F_TRY(cudaMemcpyAsync(d_qx, qx.data(), nq * sizeof(double), cudaMemcpyHostToDevice, c->s));
     F_TRY(cudaMemcpyAsync(d_qw, qw.data(), nq * sizeof(double), cudaMemcpyHostToDevice, c->s));
     k_element_weights<<<ns, 128, 0, c->s>>>(ns, ps, L, c->tree.box, F.lev[L].s, F.lev[L].hs, F.lev[L].ho, c->d_xyz, c->d_tri,
-                                           c->d_xc, c->d_n, c->tree.key, nq, d_qx, d_qw, F.At, F.As, F.Dv, F.Dn);
+                                           c->d_xc, c->d_n, c->tree.key, nq, d_qx, d_qw, F.At, F.As, F.Dv, F.Dn, F.fft);
     F_TRY(cudaGetLastError());
 
     // time tables of a leaf interval: source position t (sigma = k Lt + t)
@@ -1530,7 +1546,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     std::vector<double> tl((size_t)F.Lt * 8, 0.0), dtl((size_t)F.Lt * 8, 0.0);
     for (int t = 0; t < F.Lt; ++t) {
         double v[kMaxP], dv[kMaxP];
-        h_lagrange(pt, (2.0 * t - (F.Lt - 1)) / F.Lt, v, dv);
+        h_lagrange(pt, (2.0 * t - (F.Lt - 1)) / F.Lt, v, dv, F.fft);
         for (int m = 0; m < pt; ++m) {
             tl[t * 8 + m] = v[m];
             dtl[t * 8 + m] = dv[m] / (F.Lt * c->P.dt / 2.0);
@@ -1555,13 +1571,13 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
     for (int h = 0; h < 2; ++h)
         for (int n = 0; n < pt; ++n) {
             double v[kMaxP];
-            h_lagrange(pt, (h_cheb(pt, n) + 2.0 * h - 1.0) / 2.0, v, nullptr);
+            h_lagrange(pt, (h_node(pt, n, F.fft) + 2.0 * h - 1.0) / 2.0, v, nullptr, F.fft);
             for (int np_ = 0; np_ < pt; ++np_) tm[h * pt * pt + np_ * pt + n] = v[np_];
         }
     F_TRY(falloc(c, &F.Tm, tm.size()));
     {
         std::vector<double> wt(pt);
-        for (int n = 0; n < pt; ++n) wt[n] = h_cheb(pt, n);
+        for (int n = 0; n < pt; ++n) wt[n] = h_node(pt, n, F.fft);
         F_TRY(falloc(c, &F.wt, wt.size()));
         F_TRY(cudaMemcpyAsync(F.wt, wt.data(), wt.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
     }
@@ -1588,7 +1604,7 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                 for (int pos = 0; pos < 2; ++pos)
                     for (int b = 0; b < ps; ++b) {
                         double v[kMaxP];
-                        h_lagrange(ps, ((pos - 0.5) * V.s + hc * h_cheb(ps, b)) / hp, v, nullptr);
+                        h_lagrange(ps, ((pos - 0.5) * V.s + hc * h_node(ps, b, F.fft)) / hp, v, nullptr, F.fft);
                         for (int bp = 0; bp < ps; ++bp) sm[pos * ps * ps + bp * ps + b] = v[bp];
                     }
                 double **dst = kind ? &V.So : &V.Sm;
@@ -1600,6 +1616,10 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         // their offset (classes by canonical offset code, pairs by observation
         // cell and list position), and per observation cell in list order
         std::vector<int32_t> codes;  // canonical offset of each class
+        // FFT form: per pair in observation-cell order, source cell and the
+        // index of its offset S - O among the level's distinct offsets
+        std::vector<int32_t> fpS, fcodes;
+        std::vector<int16_t> fpo;
         {
             const TreeLevel &T = c->tree.levels[l];
             std::vector<int32_t> cnt(V.nc), il((size_t)V.nc * 189);
@@ -1624,6 +1644,16 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                     pcls.push_back(code);
                     pgrp.push_back(g);
                     used[code] = 1;
+                    if (F.fft) {
+                        const int oc = (o[0] + 3) + 7 * ((o[1] + 3) + 7 * (o[2] + 3));
+                        auto it = std::find(fcodes.begin(), fcodes.end(), oc);
+                        if (it == fcodes.end()) {
+                            fcodes.push_back(oc);
+                            it = fcodes.end() - 1;
+                        }
+                        fpS.push_back(S);
+                        fpo.push_back((int16_t)(it - fcodes.begin()));
+                    }
                 }
             std::vector<int> cls_of(343, -1);
             for (int code = 0; code < 343; ++code)
@@ -1669,26 +1699,29 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
         V.Tlen = c->P.c * Tdt;
         if (V.np > 0) {
             // canonical operator stacks of the level's classes (FP64)
+            // (not in the FFT form, whose blocks are applied as spectra)
             const size_t nop = (size_t)V.ncls * F.R * P;
             double *op = nullptr;
             int32_t *d_codes = nullptr;
-            F_TRY(falloc(c, &op, nop));
             F_TRY(falloc(c, &d_codes, (size_t)V.ncls));
             F_TRY(cudaMemcpyAsync(d_codes, codes.data(), V.ncls * sizeof(int32_t), cudaMemcpyHostToDevice, c->s));
-            k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, F.ngb, V.s, V.hs, V.ho, Tdt, c->P.dt, Tdt / 2.0,
-                                                        c->P.c, V.ncls, d_codes, op);
-            F_TRY(cudaGetLastError());
+            if (!F.fft) {
+                F_TRY(falloc(c, &op, nop));
+                k_m2l_operators<<<152 * 32, 256, 0, c->s>>>(ps, pt, d, F.mu, F.ngb, V.s, V.hs, V.ho, Tdt, c->P.dt,
+                                                            Tdt / 2.0, c->P.c, V.ncls, d_codes, op, F.fft);
+                F_TRY(cudaGetLastError());
+            }
             // distance powers of the derivative rows (Eq. U_expand)
             const size_t nkr = (size_t)V.ncls * (d + 1) * P3 * P3;
             if (c->split) {
                 float2 *kr = nullptr;
                 F_TRY(falloc(c, &kr, nkr));
-                k_dist_powers<float2><<<152 * 8, 256, 0, c->s>>>(V.ncls, ps, d, V.s, V.hs, V.ho, d_codes, kr);
+                k_dist_powers<float2><<<152 * 8, 256, 0, c->s>>>(V.ncls, ps, d, V.s, V.hs, V.ho, d_codes, kr, F.fft);
                 V.kr = kr;
             } else {
                 double *kr = nullptr;
                 F_TRY(falloc(c, &kr, nkr));
-                k_dist_powers<double><<<152 * 8, 256, 0, c->s>>>(V.ncls, ps, d, V.s, V.hs, V.ho, d_codes, kr);
+                k_dist_powers<double><<<152 * 8, 256, 0, c->s>>>(V.ncls, ps, d, V.s, V.hs, V.ho, d_codes, kr, F.fft);
                 V.kr = kr;
             }
             F_TRY(cudaGetLastError());
@@ -1706,13 +1739,16 @@ cudaError_t fmm_setup(tdbem_ctx *c, std::string &why)
                         jobs.push_back(make_int4(ci, (int)c0, (int)std::min<int64_t>(kDerivCols, V.cbase[ci + 1] - c0), 0));
                 V.njobs = (int)jobs.size();
                 const double A = c->P.c * ((F.mu + 1) * Tdt + c->P.dt), cht = c->P.c * Tdt / 2.0;
-                std::vector<double> tab = deriv_coef_table(d, pt, A, cht);
+                std::vector<double> tab = deriv_coef_table(d, pt, A, cht, F.fft);
                 F_TRY(falloc(c, &V.dcoef, tab.size()));
                 F_TRY(cudaMemcpyAsync(V.dcoef, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
                 F_TRY(falloc(c, &V.djobs, std::max<size_t>(jobs.size(), 1)));
                 F_TRY(cudaMemcpyAsync(V.djobs, jobs.data(), jobs.size() * sizeof(int4), cudaMemcpyHostToDevice, c->s));
             }
-            if (!c->split) {
+            if (F.fft) {
+                F_TRY(fft_m2l_level_setup(c, V, fpS, fpo, fcodes, Tdt, why));
+                if (!why.empty()) return cudaSuccess;
+            } else if (!c->split) {
                 V.op = op;
                 F_TRY(falloc(c, &V.Bbuf, (size_t)V.np * P));
                 F_TRY(falloc(c, &V.Cbuf, (size_t)V.np * F.R));
@@ -1807,53 +1843,68 @@ static cudaError_t fmm_boundary_part(tdbem_ctx *c, int k, bool graph, int part)
         if (V.np > 0) {
             cudaEvent_t ev = nullptr;
             if (!graph) phase_begin(c, &ev);
-            if (urgent) {
-                const int64_t n = V.np * P;
-                const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-                if (!graph) c->far_kernels += 1;
-                if (F.f16) {
-                    k_cell_scale<<<V.nc, 256, 0, s>>>(P, V.M, V.cexp, w);
-                    k_m2l_gather_f16<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, V.pS, V.pg, F.perm, V.M, V.cexp, V.Bt,
-                                                         V.bscale, w);
-                } else if (c->split)
-                    k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M, V.Bt,
-                                                            w);
-                else
-                    k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf, w);
-                F_TRY(cudaGetLastError());
-            }
-            // GEMM tiles: all (FB_ALL), or those of the first block / the rest
-            const int gsel = (part == FB_ALL) ? 0 : (urgent ? 1 : 2);
-            if (graph) {
-                F_TRY(m2l_products(c, V, w, gsel));
-            } else {
-                cudaEvent_t eg;
-                phase_begin(c, &eg);
-                F_TRY(m2l_products(c, V, w, gsel));
-                phase_end(c, PH_GEMM, eg);
-                c->launches[PH_GEMM] += c->split ? 1 : (gsel == 2 ? 0 : V.ncls);
-                c->gemm_tc_flops += (gsel == 0 ? V.flops_app : gsel == 1 ? V.flops_u : V.flops_app - V.flops_u) *
-                                    (c->split ? F.nprod : 1);
-            }
-            if (!graph) c->far_kernels += 1;
-            if (c->split) {
-                // rows [0, P): the first block (urgent); [P, R): blocks 2..mu
-                const int rb = urgent ? 0 : P, re = deferred ? F.R : P;
-                if (re > rb) {
-                    const int nrow = reduce_rows(F.P3, re - rb);
-                    const size_t rshm = 2 * sizeof(float) * (size_t)nrow;
-                    if (rshm > 48 * 1024)
-                        F_TRY(cudaFuncSetAttribute(k_m2l_reduce_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)rshm));
-                    k_m2l_reduce_smem<<<dim3(V.nc, (re - rb + nrow - 1) / nrow), 512, rshm, s>>>(
-                        V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, nrow, rb, re, V.ooff, V.oidx, V.og, F.perm, V.C32,
-                        V.ring, w);
+            if (F.fft) {
+                // FFT form: spectra of the moments (urgent), then the products
+                // and inverse transforms of the first block (urgent) or of
+                // blocks 2..mu (deferred), added into the ring of locals
+                cudaEvent_t eg = nullptr;
+                if (!graph) phase_begin(c, &eg);
+                if (urgent) F_TRY(fft_m2l_forward(c, V, s, w));
+                F_TRY(fft_m2l_apply(c, V, kl, urgent ? 0 : 1, deferred ? F.ngb : 1, s, w));
+                if (!graph) {
+                    phase_end(c, PH_GEMM, eg);
+                    c->launches[PH_GEMM] += 1;
+                    c->far_kernels += (urgent ? 1 : 0) + 2;
                 }
             } else {
-                k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx,
-                                                          V.og, F.iperm, V.Cbuf, V.ring, V.G, w);
+                if (urgent) {
+                    const int64_t n = V.np * P;
+                    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+                    if (!graph) c->far_kernels += 1;
+                    if (F.f16) {
+                        k_cell_scale<<<V.nc, 256, 0, s>>>(P, V.M, V.cexp, w);
+                        k_m2l_gather_f16<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, V.pS, V.pg, F.perm, V.M, V.cexp,
+                                                             V.Bt, V.bscale, w);
+                    } else if (c->split)
+                        k_m2l_gather_split<<<grid, 256, 0, s>>>(V.np, F.P3, P, F.Kp, F.ntb, V.pS, V.pg, F.perm, V.M,
+                                                                V.Bt, w);
+                    else
+                        k_m2l_gather<<<grid, 256, 0, s>>>(V.np, F.P3, P, V.pS, V.pg, F.perm, V.M, V.Bbuf, w);
+                    F_TRY(cudaGetLastError());
+                }
+                // GEMM tiles: all (FB_ALL), or those of the first block / the rest
+                const int gsel = (part == FB_ALL) ? 0 : (urgent ? 1 : 2);
+                if (graph) {
+                    F_TRY(m2l_products(c, V, w, gsel));
+                } else {
+                    cudaEvent_t eg;
+                    phase_begin(c, &eg);
+                    F_TRY(m2l_products(c, V, w, gsel));
+                    phase_end(c, PH_GEMM, eg);
+                    c->launches[PH_GEMM] += c->split ? 1 : (gsel == 2 ? 0 : V.ncls);
+                    c->gemm_tc_flops += (gsel == 0 ? V.flops_app : gsel == 1 ? V.flops_u : V.flops_app - V.flops_u) *
+                                        (c->split ? F.nprod : 1);
+                }
+                if (!graph) c->far_kernels += 1;
+                if (c->split) {
+                    // rows [0, P): the first block (urgent); [P, R): blocks 2..mu
+                    const int rb = urgent ? 0 : P, re = deferred ? F.R : P;
+                    if (re > rb) {
+                        const int nrow = reduce_rows(F.P3, re - rb);
+                        const size_t rshm = 2 * sizeof(float) * (size_t)nrow;
+                        if (rshm > 48 * 1024)
+                            F_TRY(cudaFuncSetAttribute(k_m2l_reduce_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)rshm));
+                        k_m2l_reduce_smem<<<dim3(V.nc, (re - rb + nrow - 1) / nrow), 512, rshm, s>>>(
+                            V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, nrow, rb, re, V.ooff, V.oidx, V.og, F.perm, V.C32,
+                            V.ring, w);
+                    }
+                } else {
+                    k_m2l_reduce<double><<<V.nc, 256, 0, s>>>(V.nc, F.P3, P, F.ngb, F.mu, F.nslot, kl, V.ooff, V.oidx,
+                                                              V.og, F.iperm, V.Cbuf, V.ring, V.G, w);
+                }
+                F_TRY(cudaGetLastError());
             }
-            F_TRY(cudaGetLastError());
             // the block L_{k+mu+1,k} and the derivative contributions G (exact
             // low-rank form of Eq. U_expand): moments now, the rest deferred
             const int dparts = (urgent ? 1 : 0) | (deferred ? 2 : 0);

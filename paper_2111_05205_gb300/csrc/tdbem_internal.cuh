@@ -207,6 +207,14 @@ struct FmmLevel {
     CUtensorMap mapA{}, mapB{};
     double flops_app = 0;        // algorithmic flops of one application's GEMMs: 2 P per kept operator row and pair
     double flops_deriv = 0;      // and of its derivative rows: 2 P3^2 per spatial product and pair
+    // FFT form: pairs per observation cell in interaction-list order (CSR ooff)
+    int32_t *fS = nullptr;       // [np] source cell of each pair
+    int16_t *fo = nullptr;       // [np] its offset's index into the spectra
+    int nfo = 0;                 // distinct offsets of the level
+    int fC = 0;                  // frequencies per CTA of the products
+    float2 *Khat = nullptr;      // [nfo][mu][fN] spectra of the circulant kernel samples, near future 1..mu
+    float2 *Mhat = nullptr;      // [nc][fN] spectra of the moments of the current source interval
+    float2 *Yhat = nullptr;      // [nc][mu][fN] products summed over each cell's interaction list
 };
 
 struct Fmm {
@@ -217,6 +225,9 @@ struct Fmm {
     int R = 0, Rp = 0, Kp = 0;              // their rows ngb P, rows padded to 128, K padded to 64
     int nta = 0, ntb = 0, nprod = 0;        // tensor-core forms: split terms and products
     bool f16 = false;                       // precision 4: two FP16 terms with power-of-two scales
+    bool fft = false;                       // precision 5: M2L blocks by the FFT (equispaced nodes, equal boxes)
+    int fNs = 0, fNt = 0;                   // FFT form: grid points per spatial axis and in time
+    int64_t fN = 0;                         // FFT form: grid points of one transform, fNs^3 fNt
     int prod[kTcMaxProd] = {0};
     int16_t *perm = nullptr;                // [48][P3] node permutation of each symmetry element
     int16_t *iperm = nullptr;               // [48][P3] its inverse
@@ -226,7 +237,7 @@ struct Fmm {
     double *tl = nullptr, *dtl = nullptr;  // [Lt][8] time basis at the interval's positions
     double *wk = nullptr;                   // [d+2] w^{kappa,d}
     double *Tm = nullptr;                   // [2][pt][pt] time transfer
-    double *wt = nullptr;                   // [pt] Chebyshev time nodes
+    double *wt = nullptr;                   // [pt] time nodes (Chebyshev, or equispaced in the FFT form)
     double *far = nullptr;                  // [Lt][ns] far field of the current leaf interval
     double *Tq = nullptr, *Tu = nullptr;    // [ns][pt] P2M time sums of the folded histories (sorted order)
     int far_k = -1;                         // leaf interval the far field belongs to
@@ -370,6 +381,11 @@ cudaError_t build_near_lists(tdbem_ctx *c);
 cudaError_t fmm_setup(tdbem_ctx *c, std::string &why);
 cudaError_t fmm_boundary(tdbem_ctx *c, int k, bool graph = false);
 cudaError_t fmm_join(tdbem_ctx *c);
+cudaError_t fft_m2l_level_setup(tdbem_ctx *c, FmmLevel &V, const std::vector<int32_t> &pS,
+                                const std::vector<int16_t> &po, const std::vector<int32_t> &codes, double Tdt,
+                                std::string &why);
+cudaError_t fft_m2l_forward(tdbem_ctx *c, FmmLevel &V, cudaStream_t s, const StepWhen &w);
+cudaError_t fft_m2l_apply(tdbem_ctx *c, FmmLevel &V, int kl, int lb, int le, cudaStream_t s, const StepWhen &w);
 // Phase timer hooks for fmm.cu (events on the context's stream).
 void phase_begin(tdbem_ctx *c, cudaEvent_t *e);
 void phase_end(tdbem_ctx *c, int phase, cudaEvent_t e);

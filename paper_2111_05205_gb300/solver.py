@@ -23,7 +23,8 @@ class Solver:
     ``stream``: a cudaStream_t handle (int) or None.  ``precision``: 0 /
     "fp64" or 1 / "split" (float-pair double-float history sum; FMM M2L with
     BF16 x 3 terms), 2 / "bf16x3", 3 / "bf16" (cheaper M2L products), 4 /
-    "f16x2" (two scaled FP16 terms, three products).
+    "f16x2" (two scaled FP16 terms, three products), 5 / "fft" (near-future
+    M2L blocks by the FFT on equispaced nodes, FP32).
     ``precond``: 0 Jacobi zero-lag solve, 1 allow a learned SAI
     (tdbem_set_precond).
     """
@@ -34,7 +35,7 @@ class Solver:
         p.c, p.dt, p.nt, p.d = float(c), float(dt), int(nt), int(d)
         p.bie = {"obie": 0, "bmbie": 1}[bie] if isinstance(bie, str) else int(bie)
         p.algo = 0
-        p.precision = {"fp64": 0, "split": 1, "bf16x3": 2, "bf16": 3, "f16x2": 4}.get(precision, precision)
+        p.precision = {"fp64": 0, "split": 1, "bf16x3": 2, "bf16": 3, "f16x2": 4, "fft": 5}.get(precision, precision)
         p.depth = int(depth)
         if fmm is not None:  # (ps, pt, mu): the space-time FMM for the far part
             p.algo = 1

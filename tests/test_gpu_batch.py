@@ -110,6 +110,8 @@ FMM_CASES = [
     ("sphere1280_bmbie_d2_neumann_uniform", 3, (2, 2, 0), 1, 81),
     ("sphere1280_bmbie_d1_dirichlet_uniform", 3, (3, 3, 0), 2, 40),
     ("ellipsoid320_bmbie_d2_hard_plane_s7", 2, (3, 3, 0), 1, 37),
+    # the FFT form of the M2L
+    ("sphere1280_bmbie_d2_neumann_uniform", 3, (2, 2, 0), 5, 81),
 ]
 
 
@@ -221,17 +223,18 @@ def test_batch_of_uneven_nt():
             s.close()
 
 
-def test_overlapped_far_field_equals_sequential():
+@pytest.mark.parametrize("precision", [4, 5])
+def test_overlapped_far_field_equals_sequential(precision):
     """Plain FMM stepping runs the part of each boundary's far-field work
     that only later boundaries need on a second stream, beside the following
     steps; the sequential schedule (tdbem_set_overlap 0) gives the same
     history bit for bit, also when the schedule changes mid-march and across
-    checkpoint/restore."""
+    checkpoint/restore (scaled FP16 GEMM form and FFT form)."""
     _need_gpu()
     from paper_2111_05205_gb300 import abi
     w = case("sphere1280_bmbie_d2_neumann_uniform", nt=81)
-    a = gpu_solver(w, precision=4, depth=3, fmm=(3, 3, 0))
-    b = gpu_solver(w, precision=4, depth=3, fmm=(3, 3, 0))
+    a = gpu_solver(w, precision=precision, depth=3, fmm=(3, 3, 0))
+    b = gpu_solver(w, precision=precision, depth=3, fmm=(3, 3, 0))
     try:
         abi.tdbem_set_overlap(b.ctx, 0)
         abi.tdbem_step(a.ctx, 40)

@@ -62,20 +62,26 @@ def _tol(precision, w, nsteps):
         by 10 % or more, which the precision table in the design notes
         records;
       precision 4 (two FP16 terms scaled per row / per cell, ~2^-22, three
-        products, FP32 accumulation): the bounds of precision 1."""
+        products, FP32 accumulation): the bounds of precision 1;
+      precision 5 (FFT form, equispaced nodes: FP32 transforms and
+        products, ~6e-8 per operation times the log of the grid size): the
+        bounds of precision 1 (measured 3.1e-3 on the 37-step d = 2 case,
+        6.5e-5 and 1.8e-7 on the 81-step ones, <= 3.5e-7 for d = 1)."""
     if precision == 0:
         return 1e-9
-    if precision in (1, 4):
+    if precision in (1, 4, 5):
         return 1e-1 if (w.d >= 2 and nsteps > 40) else 1e-2
     return 1e-5 if precision == 2 else 1e-2
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("name,L,p,nsteps", CASES)
 def test_fmm_far_field_matches_oracle(name, L, p, nsteps, precision):
     """precision 0: FP64 M2L; 1-4: M2L on the tcgen05 tensor cores with the
     operators and moments split into BF16 (1-3) or scaled FP16 (4) terms
-    (FP64 locals and recurrence state).  Tolerances: see _tol."""
+    (FP64 locals and recurrence state); 5: the near-future blocks by the FFT
+    on equispaced nodes, against the oracle's hierarchy with the same nodes
+    and boxes.  Tolerances: see _tol."""
     _need_gpu()
     from paper_2111_05205_gb300 import abi
     from tests.gpu_cases import gpu_solver
@@ -83,9 +89,10 @@ def test_fmm_far_field_matches_oracle(name, L, p, nsteps, precision):
     if precision in (2, 3) and w.d >= 2:
         pytest.skip("BF16x3 / BF16 M2L far fields are not accurate for d = 2 (see _tol)")
     s = gpu_solver(w, depth=L, fmm=(p, p, 0), precision=precision)
+    nodes = "equi" if precision == 5 else "cheb"
     try:
         st = s.stats()
-        H = ofmm.Hierarchy(w.xyz, w.tri, L, w.c, w.dt, w.nt, p, p, w.d)
+        H = ofmm.Hierarchy(w.xyz, w.tri, L, w.c, w.dt, w.nt, p, p, w.d, nodes=nodes)
         assert (st["fmm_lt"], st["fmm_mu"]) == (H.Lt, H.mu)
         # near lists bit-exact with the oracle's leaf neighbour lists
         off = abi.tdbem_get_tree(s.ctx, "near_off")
@@ -98,7 +105,7 @@ def test_fmm_far_field_matches_oracle(name, L, p, nsteps, precision):
         u, q = s.solution(0, nsteps)
         rows = list(range(0, w.ns, max(1, w.ns // 12)))
         alphas = [a0 + t for t in range(H.Lt)]
-        ref = ofmm.far_field(H, u, q, alphas, w.bie, rows=rows)
+        ref = ofmm.far_field(H, u, q, alphas, w.bie, rows=rows, m2l=ofmm.m2l_fft if precision == 5 else None)
         got = far[:, rows]
         scale = np.abs(ref).max()
         assert scale > 0
@@ -118,7 +125,7 @@ def test_fmm_infeasible_hierarchy_is_reported():
     assert e.value.code == -7
 
 
-@pytest.mark.parametrize("precision", [0, 1, 4])
+@pytest.mark.parametrize("precision", [0, 1, 4, 5])
 @pytest.mark.parametrize("p", [4, 5])
 def test_fmm_depth4_far_field_two_intervals(p, precision):
     """Depth 4 (levels 2-4 with interaction pairs, every symmetry class of
@@ -128,14 +135,16 @@ def test_fmm_depth4_far_field_two_intervals(p, precision):
     runs stay in the near-future regime where rounding is not yet amplified,
     so the bounds are tighter than _tol's: FP64 1e-10 (measured <= 1.3e-14),
     the tensor-core forms 1e-4 (measured <= 5.4e-6 for precision 1 and
-    <= 2.9e-6 for precision 4)."""
+    <= 2.9e-6 for precision 4), the FFT form's FP32 transforms 1e-3
+    (measured <= 4.4e-5 at p = 4 and <= 2.9e-4 at p = 5)."""
     _need_gpu()
     from paper_2111_05205_gb300 import abi
     from tests.gpu_cases import gpu_solver
     w = workload("ellipsoid5120_bmbie_d2_hard_plane_s3", nt=34)
     L = 4
-    tol = 1e-10 if precision == 0 else 1e-4
-    H = ofmm.Hierarchy(w.xyz, w.tri, L, w.c, w.dt, w.nt, p, p, w.d)
+    tol = 1e-10 if precision == 0 else 1e-3 if precision == 5 else 1e-4
+    nodes = "equi" if precision == 5 else "cheb"
+    H = ofmm.Hierarchy(w.xyz, w.tri, L, w.c, w.dt, w.nt, p, p, w.d, nodes=nodes)
     s = gpu_solver(w, depth=L, fmm=(p, p, 0), precision=precision)
     try:
         st = s.stats()
@@ -154,7 +163,7 @@ def test_fmm_depth4_far_field_two_intervals(p, precision):
             far, a0 = abi.tdbem_get_far(s.ctx, w.ns)
             u, q = s.solution(0, nsteps)
             alphas = [a0 + t for t in range(H.Lt)]
-            ref = ofmm.far_field(H, u, q, alphas, w.bie, rows=rows)
+            ref = ofmm.far_field(H, u, q, alphas, w.bie, rows=rows, m2l=ofmm.m2l_fft if precision == 5 else None)
             scale = np.abs(ref).max()
             assert scale > 0
             err = np.abs(far[:, rows] - ref).max() / scale
