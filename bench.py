@@ -12,8 +12,9 @@ Gaussian plane pulse (sigma = 0.3, seeded direction), Nt = 1024.  The FMM
 runs at octree depth 3 with ps = 7, pt = 8 interpolation points and the M2L
 in two scaled FP16 terms by default (the fastest configuration measured
 whose whole march stays within 1e-3 of the direct path); the configuration
-table's depth 5 with orders 5/5, depth 4 with 6/6 and depth 3 with 8/8 are
-measured beside it.
+table's depth 5 with orders 5/5, depth 4 with 6/6, depth 3 with 8/8 and 5/5,
+and the FFT form of the M2L (equispaced nodes) at depth 3 with 5/5 and 7/8
+are measured beside it.
 
 The timed steps are whole cycles of the FMM's interval pattern (the leaf
 interval times 2^(depth-2) steps, so that every level's M2L occurs in its
